@@ -1,0 +1,310 @@
+// Vector kernels of the Krylov solvers: the fused CG update (x += alpha p, p = r + beta p,
+// u = D+ p), precision casts with a scale and a fused dot product, and small vector ops.
+// All use CTA = 32 sites x Ls slices so that reductions are segmented per lattice block
+// exactly like the operator stages (segment = CTA index / (Vhb_pad / 32)).
+#include "dwf_internal.h"
+
+namespace dwf {
+
+// Grid completion without data: returns true in every thread of the last CTA to finish.
+__device__ __forceinline__ bool last_cta(unsigned* counter, unsigned total) {
+  __shared__ unsigned is_last;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    is_last = (prev == total - 1u);
+  }
+  __syncthreads();
+  return is_last != 0u;
+}
+
+template <int P, int LS>
+__global__ void __launch_bounds__(32 * LS) vec_kernel(const VecArgs a) {
+  using A = typename Prec<P>::acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.stop && *a.stop) return;
+  const int lane = threadIdx.x, s = threadIdx.y;
+  const long site = (long)blockIdx.x * 32 + lane;
+  const int seg = blockIdx.x / a.seg_cps;
+
+  Spinor<A> p;
+  load_spinor<P>(p, a.p, a.Vp, site, s);
+  if (a.do_x) {
+    const A al = A(a.alpha[seg]);
+    Spinor<A> x;
+    load_spinor<P>(x, a.x, a.Vp, site, s);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      x.c[k].x += al * p.c[k].x;
+      x.c[k].y += al * p.c[k].y;
+    }
+    store_spinor<P>(a.x, a.Vp, site, s, x);
+  }
+  if (a.do_p) {
+    const A be = A(a.beta[seg]);
+    Spinor<A> r;
+    load_spinor<P>(r, a.r, a.Vp, site, s);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      p.c[k].x = r.c[k].x + be * p.c[k].x;
+      p.c[k].y = r.c[k].y + be * p.c[k].y;
+    }
+    store_spinor<P>(a.p, a.Vp, site, s, p);
+    round_to_storage<P>(p);
+  }
+  if (a.do_u) {
+    // u_s = db p_s + dc (P- p_{s+1} + P+ p_{s-1}),  p_{Ls} = -mf p_0, p_{-1} = -mf p_{Ls-1}
+    A* buf = reinterpret_cast<A*>(smem_raw);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      buf[(s * 24 + 2 * k) * 32 + lane] = p.c[k].x;
+      buf[(s * 24 + 2 * k + 1) * 32 + lane] = p.c[k].y;
+    }
+    __syncthreads();
+    const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
+    const A fu = (s + 1 < LS) ? A(1) : A(-a.mf), fd = (s > 0) ? A(1) : A(-a.mf);
+    const A db = A(a.db), dc = A(a.dc);
+    Spinor<A> u;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const int sn = k < 6 ? sd : su;
+      const A f = k < 6 ? fd : fu;
+      u.c[k].x = db * p.c[k].x + dc * f * buf[(sn * 24 + 2 * k) * 32 + lane];
+      u.c[k].y = db * p.c[k].y + dc * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+    }
+    store_spinor<P>(a.u, a.Vp, site, s, u);
+  }
+  if (a.red.counter) {
+    if (last_cta(a.red.counter, gridDim.x)) {
+      const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+      if (tid == 0) {
+        if (a.stop_out && a.conv_in && *a.conv_in) *a.stop_out = 1;
+        if (a.iter) *a.iter += 1;
+        a.red.counter[0] = 0u;
+      }
+    }
+  }
+}
+
+template <int P, int LS>
+static cudaError_t vec_launch(const VecArgs& a, cudaStream_t st) {
+  using A = typename Prec<P>::acc;
+  const size_t sm = a.do_u ? (size_t)LS * 24 * 32 * sizeof(A) : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(vec_kernel<P, LS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(LS * 24 * 32 * sizeof(A)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  vec_kernel<P, LS><<<dim3((unsigned)(a.Vp / 32)), dim3(32, LS), sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t vec_dispatch(const VecArgs& a, int Ls, cudaStream_t st) {
+  switch (Ls) {
+    case 4: return vec_launch<P, 4>(a, st);
+    case 6: return vec_launch<P, 6>(a, st);
+    case 8: return vec_launch<P, 8>(a, st);
+    case 10: return vec_launch<P, 10>(a, st);
+    case 12: return vec_launch<P, 12>(a, st);
+    case 16: return vec_launch<P, 16>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_vec(int prec, const VecArgs& a, int Ls, cudaStream_t st) {
+  switch (prec) {
+    case P64: return vec_dispatch<P64>(a, Ls, st);
+    case P32: return vec_dispatch<P32>(a, Ls, st);
+    case P16: return vec_dispatch<P16>(a, Ls, st);
+    default: return vec_dispatch<PB16>(a, Ls, st);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Casts between precisions: out = in * f, f = sqrt(num / *den) (or num), optionally 1/f;
+// optional reduction <dotv, out> over what was stored.
+// ---------------------------------------------------------------------------------------
+template <int PI, int PO>
+__global__ void cast_kernel(const CastArgs a) {
+  using AI = typename Prec<PI>::acc;
+  using AO = typename Prec<PO>::acc;
+  __shared__ double scratch[32];
+  if (a.stop && *a.stop) return;
+  const int lane = threadIdx.x, s = threadIdx.y;
+  const long site = (long)blockIdx.x * 32 + lane;
+  double f = a.num;
+  if (a.den) {
+    const double d = *a.den;
+    f = (d > 0.0 && isfinite(d)) ? sqrt(a.num / d) : 1.0;
+  }
+  if (a.invert) f = 1.0 / f;
+  Spinor<AI> v;
+  load_spinor<PI>(v, a.in, a.Vp, site, s);
+  Spinor<AO> w;
+#pragma unroll
+  for (int k = 0; k < 12; k++) w.c[k] = {AO((double)v.c[k].x * f), AO((double)v.c[k].y * f)};
+  store_spinor<PO>(a.out, a.Vp, site, s, w);
+  if (a.out2) store_spinor<PO>(a.out2, a.Vp, site, s, w);
+  if (a.red.partial) {
+    round_to_storage<PO>(w);
+    double acc = 0.0;
+    if (a.dotv) {
+      Spinor<AO> d;
+      load_spinor<PO>(d, a.dotv, a.Vp, site, s);
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        acc += (double)d.c[k].x * w.c[k].x + (double)d.c[k].y * w.c[k].y;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        acc += (double)w.c[k].x * w.c[k].x + (double)w.c[k].y * w.c[k].y;
+    }
+    double vv[1] = {acc};
+    grid_reduce<1>(a.red, vv, scratch);
+  }
+}
+
+template <int PI>
+static cudaError_t cast_out(int pout, const CastArgs& a, dim3 g, dim3 b, cudaStream_t st) {
+  switch (pout) {
+    case P64: cast_kernel<PI, P64><<<g, b, 0, st>>>(a); break;
+    case P32: cast_kernel<PI, P32><<<g, b, 0, st>>>(a); break;
+    case P16: cast_kernel<PI, P16><<<g, b, 0, st>>>(a); break;
+    default: cast_kernel<PI, PB16><<<g, b, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast(int pin, int pout, const CastArgs& a, int Ls, cudaStream_t st) {
+  dim3 g((unsigned)(a.Vp / 32)), b(32, Ls);
+  switch (pin) {
+    case P64: return cast_out<P64>(pout, a, g, b, st);
+    case P32: return cast_out<P32>(pout, a, g, b, st);
+    case P16: return cast_out<P16>(pout, a, g, b, st);
+    default: return cast_out<PB16>(pout, a, g, b, st);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Small vector ops.
+// ---------------------------------------------------------------------------------------
+template <int P, int PX>
+__global__ void vop_kernel(const VopArgs a) {
+  using A = typename Prec<P>::acc;
+  using AX = typename Prec<PX>::acc;
+  __shared__ double scratch[32];
+  if (a.stop && *a.stop) return;
+  const int lane = threadIdx.x, s = threadIdx.y;
+  const long site = (long)blockIdx.x * 32 + lane;
+  double acc = 0.0;
+  Spinor<A> y;
+  switch (a.op) {
+    case VOP_ZERO:
+      zero(y);
+      store_spinor<P>(a.y, a.Vp, site, s, y);
+      break;
+    case VOP_COPY:
+      load_spinor<P>(y, a.x, a.Vp, site, s);
+      store_spinor<P>(a.y, a.Vp, site, s, y);
+      break;
+    case VOP_AXPY: {
+      const double c = a.sa * (a.ap ? *a.ap : 1.0);
+      Spinor<A> x;
+      load_spinor<P>(x, a.x, a.Vp, site, s);
+      load_spinor<P>(y, a.y, a.Vp, site, s);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        y.c[k].x += A(c) * x.c[k].x;
+        y.c[k].y += A(c) * x.c[k].y;
+      }
+      store_spinor<P>(a.y, a.Vp, site, s, y);
+      break;
+    }
+    case VOP_XMY_NORM: {
+      Spinor<A> x;
+      load_spinor<P>(x, a.x, a.Vp, site, s);
+      load_spinor<P>(y, a.y, a.Vp, site, s);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        y.c[k].x = x.c[k].x - y.c[k].x;
+        y.c[k].y = x.c[k].y - y.c[k].y;
+        acc += (double)y.c[k].x * y.c[k].x + (double)y.c[k].y * y.c[k].y;
+      }
+      store_spinor<P>(a.y, a.Vp, site, s, y);
+      break;
+    }
+    case VOP_NORM: {
+      load_spinor<P>(y, a.x, a.Vp, site, s);
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        acc += (double)y.c[k].x * y.c[k].x + (double)y.c[k].y * y.c[k].y;
+      break;
+    }
+    case VOP_DOT: {
+      Spinor<A> x;
+      load_spinor<P>(x, a.x, a.Vp, site, s);
+      load_spinor<P>(y, a.y, a.Vp, site, s);
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        acc += (double)x.c[k].x * y.c[k].x + (double)x.c[k].y * y.c[k].y;
+      break;
+    }
+    case VOP_ADD_CAST: {
+      Spinor<AX> x;
+      load_spinor<PX>(x, a.x, a.Vp, site, s);
+      load_spinor<P>(y, a.y, a.Vp, site, s);
+      const double c = a.sa * (a.ap ? *a.ap : 1.0);
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        y.c[k].x += A(c * (double)x.c[k].x);
+        y.c[k].y += A(c * (double)x.c[k].y);
+      }
+      store_spinor<P>(a.y, a.Vp, site, s, y);
+      break;
+    }
+  }
+  if (a.red.partial) {
+    double vv[1] = {acc};
+    grid_reduce<1>(a.red, vv, scratch);
+  }
+}
+
+template <int P>
+static cudaError_t vop_px(int px, const VopArgs& a, dim3 g, dim3 b, cudaStream_t st) {
+  switch (px) {
+    case P64: vop_kernel<P, P64><<<g, b, 0, st>>>(a); break;
+    case P32: vop_kernel<P, P32><<<g, b, 0, st>>>(a); break;
+    case P16: vop_kernel<P, P16><<<g, b, 0, st>>>(a); break;
+    default: vop_kernel<P, PB16><<<g, b, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vop(int prec, int prec_x, const VopArgs& a, int Ls, cudaStream_t st) {
+  dim3 g((unsigned)(a.Vp / 32)), b(32, Ls);
+  if (a.op != VOP_ADD_CAST) prec_x = prec;
+  switch (prec) {
+    case P64: return vop_px<P64>(prec_x, a, g, b, st);
+    case P32: return vop_px<P32>(prec_x, a, g, b, st);
+    case P16: return vop_px<P16>(prec_x, a, g, b, st);
+    default: return vop_px<PB16>(prec_x, a, g, b, st);
+  }
+}
+
+cudaError_t launch_stage_prec(int prec, const StageArgs& a, int Ls, bool dag, bool blocked,
+                              cudaStream_t st) {
+  switch (prec) {
+    case P64: return launch_stage<P64>(a, Ls, dag, blocked, st);
+    case P32: return launch_stage<P32>(a, Ls, dag, blocked, st);
+    case P16: return launch_stage<P16>(a, Ls, dag, blocked, st);
+    default: return launch_stage<PB16>(a, Ls, dag, blocked, st);
+  }
+}
+
+}  // namespace dwf

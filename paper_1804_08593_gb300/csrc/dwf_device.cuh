@@ -1,0 +1,378 @@
+// Device-side building blocks: precision traits, complex arithmetic, site-major field
+// access, and the spin projection of the Wilson hopping term.
+//
+// Field layout (one parity of a 5D field): [s][chunk][site], each chunk 16 bytes:
+//   FP64: 12 chunks of one complex (double2), FP32: 6 chunks of two complex (float4),
+//   FP16/BF16: 3 chunks of four complex (8 halves).
+// Complex component k = spin*3 + colour.  A warp reads 32 consecutive sites of one chunk,
+// i.e. 512 contiguous bytes, so every load and store is a full-width coalesced vector access.
+//
+// Link layout (one parity of output sites): [dir][9][site] with dir = 2*mu + back; entry
+// (dir, a*3+b, x) holds U_mu(x)[a][b] for forward hops and (U_mu(x-mu)^dag)[a][b] for
+// backward hops, one complex per element (double2 / float2 / half2 / bfloat162).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwf {
+
+enum PrecId { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+
+template <int P> struct Prec;
+template <> struct Prec<P64> {
+  using acc = double;
+  using link2 = double2;
+  static constexpr int NCH = 12;   // 16-byte chunks per spinor
+  static constexpr int BYTES = 8;  // bytes per real
+};
+template <> struct Prec<P32> {
+  using acc = float;
+  using link2 = float2;
+  static constexpr int NCH = 6;
+  static constexpr int BYTES = 4;
+};
+template <> struct Prec<P16> {
+  using acc = float;
+  using link2 = __half2;
+  static constexpr int NCH = 3;
+  static constexpr int BYTES = 2;
+};
+template <> struct Prec<PB16> {
+  using acc = float;
+  using link2 = __nv_bfloat162;
+  static constexpr int NCH = 3;
+  static constexpr int BYTES = 2;
+};
+
+template <typename A> struct cx {
+  A x, y;
+};
+
+template <typename A> __device__ __forceinline__ cx<A> cmul(cx<A> a, cx<A> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * b accumulated into c
+template <typename A> __device__ __forceinline__ void cfma(cx<A>& c, cx<A> a, cx<A> b) {
+  c.x = fma(a.x, b.x, fma(-a.y, b.y, c.x));
+  c.y = fma(a.x, b.y, fma(a.y, b.x, c.y));
+}
+template <typename A> __device__ __forceinline__ cx<A> cadd(cx<A> a, cx<A> b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename A> __device__ __forceinline__ cx<A> csub(cx<A> a, cx<A> b) {
+  return {a.x - b.x, a.y - b.y};
+}
+template <typename A> __device__ __forceinline__ cx<A> mul_i(cx<A> a) { return {-a.y, a.x}; }
+template <typename A> __device__ __forceinline__ cx<A> cscale(A s, cx<A> a) {
+  return {s * a.x, s * a.y};
+}
+
+template <typename A> struct Spinor {
+  cx<A> c[12];  // index spin*3 + colour
+};
+
+// ---------------------------------------------------------------------------------------
+// Spinor load/store in the chunked site-major layout.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 h2f(uint32_t v, bool bf) {
+  if (bf) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+    return __bfloat1622float2(h);
+  }
+  __half2 h = *reinterpret_cast<__half2*>(&v);
+  return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b, bool bf) {
+  uint32_t r;
+  if (bf) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    r = *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __half2 h = __floats2half2_rn(a, b);
+    r = *reinterpret_cast<uint32_t*>(&h);
+  }
+  return r;
+}
+
+template <int P>
+__device__ __forceinline__ void load_spinor(Spinor<typename Prec<P>::acc>& out, const void* base,
+                                            long Vp, long site, int s) {
+  constexpr int NCH = Prec<P>::NCH;
+  const uint4* p = reinterpret_cast<const uint4*>(base) + ((long)s * NCH) * Vp + site;
+  if constexpr (P == P64) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      double2 v = __ldg(reinterpret_cast<const double2*>(p + k * Vp));
+      out.c[k] = {v.x, v.y};
+    }
+  } else if constexpr (P == P32) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      float4 v = __ldg(reinterpret_cast<const float4*>(p + k * Vp));
+      out.c[2 * k] = {v.x, v.y};
+      out.c[2 * k + 1] = {v.z, v.w};
+    }
+  } else {
+    constexpr bool BF = (P == PB16);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint4 v = __ldg(p + k * Vp);
+      float2 a = h2f(v.x, BF), b = h2f(v.y, BF), c = h2f(v.z, BF), d = h2f(v.w, BF);
+      out.c[4 * k] = {a.x, a.y};
+      out.c[4 * k + 1] = {b.x, b.y};
+      out.c[4 * k + 2] = {c.x, c.y};
+      out.c[4 * k + 3] = {d.x, d.y};
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void store_spinor(void* base, long Vp, long site, int s,
+                                             const Spinor<typename Prec<P>::acc>& v) {
+  constexpr int NCH = Prec<P>::NCH;
+  uint4* p = reinterpret_cast<uint4*>(base) + ((long)s * NCH) * Vp + site;
+  if constexpr (P == P64) {
+#pragma unroll
+    for (int k = 0; k < 12; k++)
+      *reinterpret_cast<double2*>(p + k * Vp) = make_double2(v.c[k].x, v.c[k].y);
+  } else if constexpr (P == P32) {
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+      *reinterpret_cast<float4*>(p + k * Vp) =
+          make_float4(v.c[2 * k].x, v.c[2 * k].y, v.c[2 * k + 1].x, v.c[2 * k + 1].y);
+  } else {
+    constexpr bool BF = (P == PB16);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint4 w;
+      w.x = f2h(v.c[4 * k].x, v.c[4 * k].y, BF);
+      w.y = f2h(v.c[4 * k + 1].x, v.c[4 * k + 1].y, BF);
+      w.z = f2h(v.c[4 * k + 2].x, v.c[4 * k + 2].y, BF);
+      w.w = f2h(v.c[4 * k + 3].x, v.c[4 * k + 3].y, BF);
+      p[k * Vp] = w;
+    }
+  }
+}
+
+template <int P>
+__device__ __forceinline__ cx<typename Prec<P>::acc> load_link(const void* base, long Vp,
+                                                                long site, int dir, int k) {
+  using L2 = typename Prec<P>::link2;
+  const L2* p = reinterpret_cast<const L2*>(base) + ((long)(dir * 9 + k)) * Vp + site;
+  if constexpr (P == P64) {
+    double2 v = __ldg(p);
+    return {v.x, v.y};
+  } else if constexpr (P == P32) {
+    float2 v = __ldg(p);
+    return {v.x, v.y};
+  } else {
+    uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(p));
+    float2 f = h2f(u, P == PB16);
+    return {f.x, f.y};
+  }
+}
+
+// Rounds a spinor to the values the storage precision would hold.
+template <int P>
+__device__ __forceinline__ void round_to_storage(Spinor<typename Prec<P>::acc>& v) {
+  if constexpr (P == P16 || P == PB16) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const float2 f = h2f(f2h(v.c[k].x, v.c[k].y, P == PB16), P == PB16);
+      v.c[k] = {f.x, f.y};
+    }
+  }
+}
+
+template <typename A> __device__ __forceinline__ void zero(Spinor<A>& s) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) s.c[k] = {A(0), A(0)};
+}
+
+// ---------------------------------------------------------------------------------------
+// One term of the Wilson hopping sum: acc += (1 + sgn*gamma_mu) U psi, using
+// (1 + sgn*gamma_mu) = [[1, sgn*B], [sgn*B^dag, 1]] in the chiral basis, so the lower two
+// spins are sgn * B^dag times the projected upper half-spinor h = psi_up + sgn*B psi_dn.
+// B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.
+// ---------------------------------------------------------------------------------------
+template <int P, int MU>
+__device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
+                                         const Spinor<typename Prec<P>::acc>& psi,
+                                         const void* links, long Vp, long site, int dir,
+                                         typename Prec<P>::acc sgn) {
+  using A = typename Prec<P>::acc;
+  cx<A> h[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const cx<A> p0 = psi.c[a], p1 = psi.c[3 + a], p2 = psi.c[6 + a], p3 = psi.c[9 + a];
+    cx<A> b0, b1;  // B psi_dn
+    if constexpr (MU == 0) {
+      b0 = mul_i(p3); b0 = {-b0.x, -b0.y};
+      b1 = mul_i(p2); b1 = {-b1.x, -b1.y};
+    } else if constexpr (MU == 1) {
+      b0 = {-p3.x, -p3.y};
+      b1 = p2;
+    } else if constexpr (MU == 2) {
+      b0 = mul_i(p2); b0 = {-b0.x, -b0.y};
+      b1 = mul_i(p3);
+    } else {
+      b0 = p2;
+      b1 = p3;
+    }
+    h[0][a] = {p0.x + sgn * b0.x, p0.y + sgn * b0.y};
+    h[1][a] = {p1.x + sgn * b1.x, p1.y + sgn * b1.y};
+  }
+  cx<A> g[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    g[0][a] = {A(0), A(0)};
+    g[1][a] = {A(0), A(0)};
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const cx<A> u = load_link<P>(links, Vp, site, dir, a * 3 + b);
+      cfma(g[0][a], u, h[0][b]);
+      cfma(g[1][a], u, h[1][b]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    acc.c[a] = cadd(acc.c[a], g[0][a]);
+    acc.c[3 + a] = cadd(acc.c[3 + a], g[1][a]);
+    cx<A> l0, l1;  // B^dag g
+    if constexpr (MU == 0) {
+      l0 = mul_i(g[1][a]);
+      l1 = mul_i(g[0][a]);
+    } else if constexpr (MU == 1) {
+      l0 = g[1][a];
+      l1 = {-g[0][a].x, -g[0][a].y};
+    } else if constexpr (MU == 2) {
+      l0 = mul_i(g[0][a]);
+      l1 = mul_i(g[1][a]); l1 = {-l1.x, -l1.y};
+    } else {
+      l0 = g[0][a];
+      l1 = g[1][a];
+    }
+    acc.c[6 + a] = {acc.c[6 + a].x + sgn * l0.x, acc.c[6 + a].y + sgn * l0.y};
+    acc.c[9 + a] = {acc.c[9 + a].x + sgn * l1.x, acc.c[9 + a].y + sgn * l1.y};
+  }
+}
+
+// Neighbour table entries: index of the neighbour in the other parity's site order; bit 31
+// marks a hop that crosses a block face (skipped by the block-local operator); bit 30 marks a
+// neighbour that lives in the block's own halo array (exact block operator).
+constexpr uint32_t NBR_FACE = 0x80000000u;
+constexpr uint32_t NBR_HALO = 0x40000000u;
+constexpr uint32_t NBR_IDX = 0x3fffffffu;
+
+// ---------------------------------------------------------------------------------------
+// Deterministic grid reduction: per-CTA partials, the last CTA of each segment sums its
+// segment's partials in a fixed order and applies a finalize operation.
+// ---------------------------------------------------------------------------------------
+enum FinOp {
+  FIN_STORE = 0,   // res[seg] = v
+  FIN_ALPHA = 1,   // alpha[seg] = rho[seg] / v   (v = <p, A p>)
+  FIN_BETA = 2,    // beta[seg] = v / rho[seg]; rho[seg] = v; conv if v <= stop2
+  FIN_NONE = 3,
+  FIN_ALPHA2 = 4   // alpha[seg] = rho[seg] / (v + extra[seg])
+};
+
+struct RedArgs {
+  double* partial;      // [gridDim.x * NV]
+  unsigned* counter;    // [nseg], zero between uses
+  int cps;              // CTAs per segment
+  int op;               // FinOp
+  double* res;          // [nseg * NV]
+  double* rho;          // [nseg]
+  double* alpha;        // [nseg]
+  double* beta;         // [nseg]
+  const double* stop2;  // stop threshold on v (segment 0 only), nullable
+  int* conv;            // set to 1 when v <= *stop2, nullable
+  const double* extra;  // FIN_ALPHA2: partial sum from a previous launch
+  double* hist;         // FIN_BETA: hist[*hist_idx] = v (nullable)
+  const int* hist_idx;
+  int hist_cap;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of NV values per thread; result valid in thread 0.  scratch: >= 32*NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; i++) v[i] = warp_sum(v[i]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NV; i++) scratch[warp * NV + i] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+      double t = lane < nw ? scratch[lane * NV + i] : 0.0;
+      v[i] = warp_sum(t);
+    }
+  }
+}
+
+template <int NV>
+__device__ void finalize_value(const RedArgs& r, int seg, const double (&v)[NV]) {
+#pragma unroll
+  for (int i = 0; i < NV; i++)
+    if (r.res) r.res[seg * NV + i] = v[i];
+  const double x = v[0];
+  if (r.op == FIN_ALPHA || r.op == FIN_ALPHA2) {
+    const double rho = r.rho[seg];
+    const double pap = r.op == FIN_ALPHA2 ? x + r.extra[seg] : x;
+    r.alpha[seg] = (pap > 0.0 && isfinite(pap)) ? rho / pap : 0.0;
+  } else if (r.op == FIN_BETA) {
+    const double rho = r.rho[seg];
+    r.beta[seg] = (rho > 0.0 && isfinite(x)) ? x / rho : 0.0;
+    r.rho[seg] = x;
+    if (r.stop2 && r.conv && (x <= *r.stop2 || !isfinite(x))) *r.conv = 1;
+    if (r.hist && *r.hist_idx < r.hist_cap) r.hist[*r.hist_idx] = x;
+  }
+}
+
+// Called by every thread of the CTA after its per-thread values are known.
+template <int NV>
+__device__ void grid_reduce(const RedArgs& r, double (&v)[NV], double* scratch) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  block_sum<NV>(v, scratch);
+  __shared__ unsigned is_last;
+  const int seg = blockIdx.x / r.cps;
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; i++) r.partial[(long)blockIdx.x * NV + i] = v[i];
+    __threadfence();
+    const unsigned prev = atomicAdd(&r.counter[seg], 1u);
+    is_last = (prev == (unsigned)r.cps - 1u);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int i = 0; i < NV; i++) s[i] = 0.0;
+  const long base = (long)seg * r.cps;
+  for (int k = tid; k < r.cps; k += nthr)
+#pragma unroll
+    for (int i = 0; i < NV; i++) s[i] += __ldcg(&r.partial[(base + k) * NV + i]);
+  block_sum<NV>(s, scratch);
+  if (tid == 0) {
+    finalize_value<NV>(r, seg, s);
+    r.counter[seg] = 0u;
+  }
+}
+
+}  // namespace dwf

@@ -1,0 +1,276 @@
+// Host-side internals of libdwf: geometry of a site ordering, packed layouts, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dwf.h"
+#include "dwf_device.cuh"
+#include "stage.cuh"
+
+namespace dwf {
+
+// Thread-local error message; set_error returns the status for convenience.
+dwf_status set_error(dwf_status st, const std::string& msg);
+dwf_status cuda_error(cudaError_t e, const char* what);
+
+#define DWF_CUDA(call)                                          \
+  do {                                                          \
+    cudaError_t _e = (call);                                    \
+    if (_e != cudaSuccess) return cuda_error(_e, #call);        \
+  } while (0)
+
+#define DWF_TRY(call)                                           \
+  do {                                                          \
+    dwf_status _s = (call);                                     \
+    if (_s != DWF_OK) return _s;                                \
+  } while (0)
+
+// A site ordering: the lattice is cut into blocks B (B = L gives one block, i.e. plain
+// checkerboard order); sites of one parity are stored block after block, each block padded
+// to a multiple of 32 sites.  Index of a parity-p site: blk * Vhb_pad + j,
+// j = (lx/2) + (Bx/2) * (ly + By * (lz + Bz * lt)) with (lx, ly, lz, lt) block-local.
+struct Geom {
+  int L[4];
+  int B[4];
+  int nb[4];
+  int nblocks;
+  int Vhb;       // sites of one parity per block
+  int Vhb_pad;   // padded to a multiple of 32
+  long Vp;       // nblocks * Vhb_pad
+  long V;        // full volume
+  int Ls;
+  bool same(const int* blk) const {
+    return B[0] == blk[0] && B[1] == blk[1] && B[2] == blk[2] && B[3] == blk[3];
+  }
+};
+
+// Halo of every block for the exact block operator P_s A P_s: the odd sites one hop outside
+// the block and the even sites up to two hops outside (Mpc P_s v is supported on the block
+// plus its even halo).  Each block owns its own halo arrays, padded to 32 sites.
+struct Halo {
+  int Ho_b = 0, Ho_pad = 0, He_b = 0, He_pad = 0;
+  long Ho_tot = 0, He_tot = 0;
+  uint32_t* nbr_be = nullptr;  // [8][Vp] block even -> odd (in block | HALO odd halo)
+  uint32_t* nbr_bo = nullptr;  // [8][Vp] block odd -> even (in block | HALO even halo)
+  uint32_t* nbr_ho = nullptr;  // [8][Ho_tot] odd halo -> even (in block | HALO | FACE absent)
+  uint32_t* nbr_he = nullptr;  // [8][He_tot] even halo -> odd (in block | HALO | FACE absent)
+  int* ls_ho = nullptr;        // [Ho_tot] odd halo site -> its odd index (links)
+  int* ls_he = nullptr;        // [He_tot] even halo site -> its even index (links)
+  ~Halo();
+};
+
+// Device tables and packed links of one site ordering.
+struct Layout {
+  std::unique_ptr<Halo> halo;              // built on demand (exact block operator)
+  Geom g;
+  uint32_t* nbr[2] = {nullptr, nullptr};   // [8][Vp] per output parity
+  int* lex[2] = {nullptr, nullptr};        // internal index -> lexicographic site (-1 = pad)
+  int* cb_even = nullptr;                  // internal even index -> caller even-half index
+  void* links[4][2] = {};                  // [precision][parity] packed links, lazily built
+  bool links_valid[4] = {false, false, false, false};
+  ~Layout();
+};
+
+// Per-chirality Ls x Ls matrices of the fifth dimension (double and float copies).
+struct Matrices {
+  // host copies in double, [2][Ls][Ls]
+  std::vector<double> dp, dpt, dpm5i, m5idpt, m5, m5t;
+  // device copies: [which][precision class: 0 double, 1 float]
+  void* d_dpm5i[2] = {};   // D+ M5op^-1 (post of stage A)
+  void* d_m5idpt[2] = {};  // M5op^-dag D+^dag (post of stage A^dag)
+  void* d_dpt[2] = {};     // D+^dag (post of stage B^dag and of D^dag)
+  void* d_dp[2] = {};      // D+ (pre-op)
+  double m5_alpha = 0, m5_beta = 0;  // M5op = alpha + beta K
+  bool dplus_trivial = true;         // c == 0 (D+ = b)
+};
+
+struct Workspace;
+
+// Event-based per-kernel profiler of a handle (off by default).
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int cls;
+    double bytes, flops;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::string> names;
+  size_t used = 0;
+  int class_id(const std::string& n) {
+    for (size_t i = 0; i < names.size(); i++)
+      if (names[i] == n) return (int)i;
+    names.push_back(n);
+    return (int)names.size() - 1;
+  }
+  cudaEvent_t ev() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// RAII bracket of one launch: records the start event at construction and the stop event
+// (with the launch's algorithmic bytes) at destruction.
+struct ProfScope {
+  Profiler* p;
+  cudaStream_t st;
+  Profiler::Rec r{};
+  ProfScope(Profiler* prof, cudaStream_t s, const char* name, double bytes, double flops)
+      : p(prof && prof->on ? prof : nullptr), st(s) {
+    if (!p) return;
+    r.cls = p->class_id(name);
+    r.bytes = bytes;
+    r.flops = flops;
+    r.a = p->ev();
+    r.b = p->ev();
+    cudaEventRecord(r.a, st);
+  }
+  ~ProfScope() {
+    if (!p) return;
+    cudaEventRecord(r.b, st);
+    p->recs.push_back(r);
+  }
+};
+
+inline const char* prec_name(int p) {
+  return p == 0 ? "f64" : p == 1 ? "f32" : p == 2 ? "f16" : "bf16";
+}
+
+}  // namespace dwf
+
+struct dwf_ctx {
+  int dims[4];
+  int Ls;
+  double M5, mf, b, c;
+  cudaStream_t stream;
+  int device;
+  double* links_c128 = nullptr;  // device copy of the caller links
+  dwf::Matrices mats;
+  std::vector<std::unique_ptr<dwf::Layout>> layouts;
+  std::unique_ptr<dwf::Workspace> ws;
+  // per-handle device scratch for reductions
+  double* red_partial = nullptr;
+  size_t red_partial_len = 0;
+  unsigned* red_counter = nullptr;
+  size_t red_counter_len = 0;
+  double* scal = nullptr;   // device scalars (see Scalars in solvers)
+  size_t scal_len = 0;
+  double* h_pinned = nullptr;  // pinned host mirror for scalar reads
+  dwf::Profiler prof;
+};
+
+namespace dwf {
+
+// ---- layouts and packing (pack.cu) ----
+dwf_status get_layout(dwf_ctx* h, const int block[4], Layout** out);
+dwf_status ensure_links(dwf_ctx* h, Layout* lay, int prec);
+dwf_status ensure_halo(dwf_ctx* h, Layout* lay);
+dwf_status build_matrices(dwf_ctx* h);
+
+// Field sizes in bytes.
+inline size_t real_bytes(int prec) { return prec == P64 ? 8 : prec == P32 ? 4 : 2; }
+inline size_t field_bytes(const Geom& g, int prec) {
+  return (size_t)g.Ls * (size_t)g.Vp * 24 * real_bytes(prec);
+}
+
+// Caller even-half c128 (device) <-> internal even field of precision prec.
+// scale: multiplies on pack, divides on unpack (FP16/BF16 range control).
+dwf_status pack_even(dwf_ctx* h, Layout* lay, const void* src_c128, void* dst, int prec,
+                     double scale);
+dwf_status unpack_even(dwf_ctx* h, Layout* lay, const void* src, int prec, void* dst_c128,
+                       double scale);
+// Caller full c128 <-> internal (even, odd) fields.
+dwf_status pack_full(dwf_ctx* h, Layout* lay, const void* src_c128, void* dst_even,
+                     void* dst_odd, int prec);
+dwf_status unpack_full(dwf_ctx* h, Layout* lay, const void* src_even, const void* src_odd,
+                       int prec, void* dst_c128);
+
+// ---- stage kernels (stage_f*.cu) ----
+template <int P>
+cudaError_t launch_stage(const StageArgs& a, int Ls, bool dag, bool blocked, cudaStream_t st);
+cudaError_t launch_stage_prec(int prec, const StageArgs& a, int Ls, bool dag, bool blocked,
+                              cudaStream_t st);
+
+// ---- vector kernels (blas.cu) ----
+struct VecArgs {
+  void* x;            // x += alpha * p         (if do_x)
+  void* p;            // p = r + beta * p       (if do_p)
+  const void* r;
+  void* u;            // u = (db + dc K) p_new  (if do_u)
+  long Vp;
+  int Vhb, Vhb_pad;
+  const double* alpha;  // per segment
+  const double* beta;   // per segment
+  int seg_cps;          // CTAs per scalar segment
+  int do_x, do_p, do_u;
+  double db, dc, mf;
+  const int* stop;
+  RedArgs red;          // with red.partial != nullptr: grid completion + finalize
+  int* stop_out;        // set *stop_out = *conv_in in the finalize (nullable)
+  const int* conv_in;
+  int* iter;            // incremented in the finalize (nullable)
+};
+cudaError_t launch_vec(int prec, const VecArgs& a, int Ls, cudaStream_t st);
+
+// Elementwise conversion out = in * f (f = sqrt(num / *den) if den else num), both fields of
+// the same geometry, with an optional reduction of <dotv, out> (dotv in out's precision).
+struct CastArgs {
+  const void* in;
+  void* out;
+  long Vp;
+  int Vhb, Vhb_pad;
+  double num;
+  const double* den;     // nullable
+  int invert;            // use 1/f
+  const void* dotv;      // nullable
+  void* out2;            // nullable: second copy of out
+  const int* stop;
+  RedArgs red;
+};
+cudaError_t launch_cast(int pin, int pout, const CastArgs& a, int Ls, cudaStream_t st);
+
+// Generic small vector ops on one precision.
+enum VOp {
+  VOP_ZERO = 0,      // y = 0
+  VOP_COPY = 1,      // y = x
+  VOP_AXPY = 2,      // y = y + a x          (a from device scalar *ap times sa)
+  VOP_XMY_NORM = 3,  // y = x - y, reduce |y|^2
+  VOP_NORM = 4,      // reduce |x|^2
+  VOP_DOT = 5,       // reduce Re <x, y>
+  VOP_ADD_CAST = 6   // y (P64) += x (other precision)   [reliable update]
+};
+struct VopArgs {
+  int op;
+  const void* x;
+  void* y;
+  long Vp;
+  int Vhb, Vhb_pad;
+  double sa;
+  const double* ap;
+  const int* stop;
+  RedArgs red;
+};
+cudaError_t launch_vop(int prec, int prec_x, const VopArgs& a, int Ls, cudaStream_t st);
+
+// ---- helpers (api.cu) ----
+dwf_status ensure_reduction(dwf_ctx* h, size_t partials, size_t counters);
+RedArgs make_red(dwf_ctx* h, int cps, int op, double* res);
+dwf_status stage_buffer(dwf_ctx* h, const char* name, const void* user, size_t bytes,
+                        bool copy_in, void** dev);
+dwf_status finish_output(dwf_ctx* h, void* user, const void* dev, size_t bytes);
+bool is_device_ptr(const void* p);
+
+}  // namespace dwf
