@@ -73,6 +73,17 @@ dwf_status finish_output(dwf_ctx* h, void* user, const void* dev, size_t bytes) 
   if (dev != user)
     DWF_CUDA(cudaMemcpyAsync(user, dev, bytes, cudaMemcpyDeviceToHost, h->stream));
   DWF_CUDA(cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
+dwf_status check_device_error(dwf_ctx* h) {
+  int e = 0;
+  DWF_CUDA(cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DWF_CUDA(cudaStreamSynchronize(h->stream));
+  if (e) {
+    DWF_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
+    return set_error(DWF_ERR_TIMEOUT, "a bounded device-side wait (tensor-core completion) gave up");
+  }
   return DWF_OK;
 }
 
@@ -122,6 +133,12 @@ dwf_status dwf_create(dwf_t* handle, const int dims[4], int Ls, double M5, doubl
     cudaGetLastError();
     dwf_destroy(h);
     return set_error(DWF_ERR_NOMEM, "links allocation failed");
+  }
+  if (cudaMalloc(&h->dev_err, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->dev_err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    dwf_destroy(h);
+    return set_error(DWF_ERR_NOMEM, "error flag allocation failed");
   }
   if (cudaMallocHost(&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -249,6 +266,8 @@ void dwf_destroy(dwf_t h) {
     cudaFree(h->mats.d_dpm5i[i]);
     cudaFree(h->mats.d_m5idpt[i]);
   }
+  for (int i = 0; i < 3; i++) cudaFree(h->mats.d_post_h[i]);
+  cudaFree(h->dev_err);
   cudaFree(h->links_c128);
   cudaFree(h->red_partial);
   cudaFree(h->red_counter);

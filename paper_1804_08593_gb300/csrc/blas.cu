@@ -2,11 +2,14 @@
 // u = D+ p), precision casts with a scale and a fused dot product, and small vector ops.
 // All use CTA = 32 sites x Ls slices so that reductions are segmented per lattice block
 // exactly like the operator stages (segment = CTA index / (Vhb_pad / 32)).
+#include <type_traits>
+
 #include "dwf_internal.h"
 
 namespace dwf {
 
-// Grid completion without data: returns true in every thread of the last CTA to finish.
+// Completion counting without data: returns true in every thread of the last CTA to finish
+// (of `total` CTAs that count on this counter).
 __device__ __forceinline__ bool last_cta(unsigned* counter, unsigned total) {
   __shared__ unsigned is_last;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -24,10 +27,20 @@ template <int P, int LS>
 __global__ void __launch_bounds__(32 * LS) vec_kernel(const VecArgs a) {
   using A = typename Prec<P>::acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (a.stop && *a.stop) return;
   const int lane = threadIdx.x, s = threadIdx.y;
   const long site = (long)blockIdx.x * 32 + lane;
-  const int seg = blockIdx.x / a.seg_cps;
+  int seg;
+  double dbv = a.db, dcv = a.dc, mfv = a.mf;
+  if (a.tile_seg) {
+    seg = a.tile_seg[blockIdx.x];
+    if (a.stop && a.stop[seg]) return;
+    dbv = a.segp[seg].db;
+    dcv = a.segp[seg].dc;
+    mfv = a.segp[seg].mf;
+  } else {
+    if (a.stop && *a.stop) return;
+    seg = blockIdx.x / a.seg_cps;
+  }
 
   Spinor<A> p;
   load_spinor<P>(p, a.p, a.Vp, site, s);
@@ -64,8 +77,8 @@ __global__ void __launch_bounds__(32 * LS) vec_kernel(const VecArgs a) {
     }
     __syncthreads();
     const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
-    const A fu = (s + 1 < LS) ? A(1) : A(-a.mf), fd = (s > 0) ? A(1) : A(-a.mf);
-    const A db = A(a.db), dc = A(a.dc);
+    const A fu = (s + 1 < LS) ? A(1) : A(-mfv), fd = (s > 0) ? A(1) : A(-mfv);
+    const A db = A(dbv), dc = A(dcv);
     Spinor<A> u;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -77,8 +90,16 @@ __global__ void __launch_bounds__(32 * LS) vec_kernel(const VecArgs a) {
     store_spinor<P>(a.u, a.Vp, site, s, u);
   }
   if (a.red.counter) {
-    if (last_cta(a.red.counter, gridDim.x)) {
-      const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (a.tile_seg) {
+      // per problem: the last tile of the problem copies its convergence flag to its stop
+      // flag and counts the iteration
+      if (last_cta(a.red.counter + seg, a.segp[seg].ntiles) && tid == 0) {
+        if (a.stop_out && a.conv_in && a.conv_in[seg]) a.stop_out[seg] = 1;
+        if (a.iter) a.iter[seg] += 1;
+        a.red.counter[seg] = 0u;
+      }
+    } else if (last_cta(a.red.counter, gridDim.x)) {
       if (tid == 0) {
         if (a.stop_out && a.conv_in && *a.conv_in) *a.stop_out = 1;
         if (a.iter) *a.iter += 1;
@@ -135,38 +156,55 @@ __global__ void cast_kernel(const CastArgs a) {
   using AI = typename Prec<PI>::acc;
   using AO = typename Prec<PO>::acc;
   __shared__ double scratch[32];
-  if (a.stop && *a.stop) return;
+  int seg = 0;
+  if (a.tile_seg) {
+    seg = a.tile_seg[blockIdx.x];
+    if (a.stop && a.stop[seg]) return;
+  } else if (a.stop && *a.stop) {
+    return;
+  }
   const int lane = threadIdx.x, s = threadIdx.y;
   const long site = (long)blockIdx.x * 32 + lane;
-  double f = a.num;
-  if (a.den) {
-    const double d = *a.den;
-    f = (d > 0.0 && isfinite(d)) ? sqrt(a.num / d) : 1.0;
+  // the scale factor is computed once per CTA (FP64 is slow on this part) and applied in
+  // the wider of the two accumulation types
+  using AW = typename std::conditional<(PI == P64 || PO == P64), double, float>::type;
+  __shared__ double fsh;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    double f = a.num;
+    if (a.den) {
+      const double d = *a.den;
+      f = (d > 0.0 && isfinite(d)) ? sqrt(a.num / d) : 1.0;
+    }
+    fsh = a.invert ? 1.0 / f : f;
   }
-  if (a.invert) f = 1.0 / f;
+  __syncthreads();
+  const AW f = AW(fsh);
   Spinor<AI> v;
   load_spinor<PI>(v, a.in, a.Vp, site, s);
   Spinor<AO> w;
 #pragma unroll
-  for (int k = 0; k < 12; k++) w.c[k] = {AO((double)v.c[k].x * f), AO((double)v.c[k].y * f)};
+  for (int k = 0; k < 12; k++) w.c[k] = {AO((AW)v.c[k].x * f), AO((AW)v.c[k].y * f)};
   store_spinor<PO>(a.out, a.Vp, site, s, w);
   if (a.out2) store_spinor<PO>(a.out2, a.Vp, site, s, w);
   if (a.red.partial) {
     round_to_storage<PO>(w);
-    double acc = 0.0;
+    AO part = AO(0);
     if (a.dotv) {
       Spinor<AO> d;
       load_spinor<PO>(d, a.dotv, a.Vp, site, s);
 #pragma unroll
-      for (int k = 0; k < 12; k++)
-        acc += (double)d.c[k].x * w.c[k].x + (double)d.c[k].y * w.c[k].y;
+      for (int k = 0; k < 12; k++) part = fma(d.c[k].x, w.c[k].x, fma(d.c[k].y, w.c[k].y, part));
     } else {
 #pragma unroll
-      for (int k = 0; k < 12; k++)
-        acc += (double)w.c[k].x * w.c[k].x + (double)w.c[k].y * w.c[k].y;
+      for (int k = 0; k < 12; k++) part = fma(w.c[k].x, w.c[k].x, fma(w.c[k].y, w.c[k].y, part));
     }
+    const double acc = (double)part;
     double vv[1] = {acc};
-    grid_reduce<1>(a.red, vv, scratch);
+    if (a.tile_seg)
+      grid_reduce_seg<1>(a.red, vv, scratch, blockIdx.x, seg, a.segp[seg].first_tile,
+                         a.segp[seg].ntiles);
+    else
+      grid_reduce<1>(a.red, vv, scratch);
   }
 }
 
@@ -199,7 +237,13 @@ __global__ void vop_kernel(const VopArgs a) {
   using A = typename Prec<P>::acc;
   using AX = typename Prec<PX>::acc;
   __shared__ double scratch[32];
-  if (a.stop && *a.stop) return;
+  int seg = 0;
+  if (a.tile_seg) {
+    seg = a.tile_seg[blockIdx.x];
+    if (a.stop && a.stop[seg]) return;
+  } else if (a.stop && *a.stop) {
+    return;
+  }
   const int lane = threadIdx.x, s = threadIdx.y;
   const long site = (long)blockIdx.x * 32 + lane;
   double acc = 0.0;
@@ -231,28 +275,32 @@ __global__ void vop_kernel(const VopArgs a) {
       load_spinor<P>(x, a.x, a.Vp, site, s);
       load_spinor<P>(y, a.y, a.Vp, site, s);
 #pragma unroll
+      A part = A(0);
       for (int k = 0; k < 12; k++) {
         y.c[k].x = x.c[k].x - y.c[k].x;
         y.c[k].y = x.c[k].y - y.c[k].y;
-        acc += (double)y.c[k].x * y.c[k].x + (double)y.c[k].y * y.c[k].y;
+        part = fma(y.c[k].x, y.c[k].x, fma(y.c[k].y, y.c[k].y, part));
       }
+      acc = (double)part;
       store_spinor<P>(a.y, a.Vp, site, s, y);
       break;
     }
     case VOP_NORM: {
       load_spinor<P>(y, a.x, a.Vp, site, s);
+      A part = A(0);
 #pragma unroll
-      for (int k = 0; k < 12; k++)
-        acc += (double)y.c[k].x * y.c[k].x + (double)y.c[k].y * y.c[k].y;
+      for (int k = 0; k < 12; k++) part = fma(y.c[k].x, y.c[k].x, fma(y.c[k].y, y.c[k].y, part));
+      acc = (double)part;
       break;
     }
     case VOP_DOT: {
       Spinor<A> x;
       load_spinor<P>(x, a.x, a.Vp, site, s);
       load_spinor<P>(y, a.y, a.Vp, site, s);
+      A part = A(0);
 #pragma unroll
-      for (int k = 0; k < 12; k++)
-        acc += (double)x.c[k].x * y.c[k].x + (double)x.c[k].y * y.c[k].y;
+      for (int k = 0; k < 12; k++) part = fma(x.c[k].x, y.c[k].x, fma(x.c[k].y, y.c[k].y, part));
+      acc = (double)part;
       break;
     }
     case VOP_ADD_CAST: {
@@ -271,7 +319,11 @@ __global__ void vop_kernel(const VopArgs a) {
   }
   if (a.red.partial) {
     double vv[1] = {acc};
-    grid_reduce<1>(a.red, vv, scratch);
+    if (a.tile_seg)
+      grid_reduce_seg<1>(a.red, vv, scratch, blockIdx.x, seg, a.segp[seg].first_tile,
+                         a.segp[seg].ntiles);
+    else
+      grid_reduce<1>(a.red, vv, scratch);
   }
 }
 

@@ -7,9 +7,10 @@
 // Complex component k = spin*3 + colour.  A warp reads 32 consecutive sites of one chunk,
 // i.e. 512 contiguous bytes, so every load and store is a full-width coalesced vector access.
 //
-// Link layout (one parity of output sites): [dir][9][site] with dir = 2*mu + back; entry
-// (dir, a*3+b, x) holds U_mu(x)[a][b] for forward hops and (U_mu(x-mu)^dag)[a][b] for
-// backward hops, one complex per element (double2 / float2 / half2 / bfloat162).
+// Link layout (one parity of output sites): [dir][chunk][site] with dir = 2*mu + back and
+// 16-byte chunks holding the 9 complex elements k = a*3+b of U_mu(x) (forward hops) or
+// U_mu(x-mu)^dag (backward hops) in order: FP64 9 chunks of one complex, FP32 5 chunks of
+// two (the last half-empty), FP16/BF16 3 chunks of four (the last 3/4 empty).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -26,24 +27,28 @@ template <> struct Prec<P64> {
   using acc = double;
   using link2 = double2;
   static constexpr int NCH = 12;   // 16-byte chunks per spinor
+  static constexpr int NCHL = 9;   // 16-byte chunks per link
   static constexpr int BYTES = 8;  // bytes per real
 };
 template <> struct Prec<P32> {
   using acc = float;
   using link2 = float2;
   static constexpr int NCH = 6;
+  static constexpr int NCHL = 5;
   static constexpr int BYTES = 4;
 };
 template <> struct Prec<P16> {
   using acc = float;
   using link2 = __half2;
   static constexpr int NCH = 3;
+  static constexpr int NCHL = 3;
   static constexpr int BYTES = 2;
 };
 template <> struct Prec<PB16> {
   using acc = float;
   using link2 = __nv_bfloat162;
   static constexpr int NCH = 3;
+  static constexpr int NCHL = 3;
   static constexpr int BYTES = 2;
 };
 
@@ -157,21 +162,40 @@ __device__ __forceinline__ void store_spinor(void* base, long Vp, long site, int
   }
 }
 
+// The 9 complex elements of one link (16-byte vector loads).
 template <int P>
-__device__ __forceinline__ cx<typename Prec<P>::acc> load_link(const void* base, long Vp,
-                                                                long site, int dir, int k) {
-  using L2 = typename Prec<P>::link2;
-  const L2* p = reinterpret_cast<const L2*>(base) + ((long)(dir * 9 + k)) * Vp + site;
+__device__ __forceinline__ void load_link9(cx<typename Prec<P>::acc> (&u)[9], const void* base,
+                                           long Vp, long site, int dir) {
+  constexpr int NCHL = Prec<P>::NCHL;
+  const uint4* p = reinterpret_cast<const uint4*>(base) + (long)dir * NCHL * Vp + site;
   if constexpr (P == P64) {
-    double2 v = __ldg(p);
-    return {v.x, v.y};
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(p + k * Vp));
+      u[k] = {v.x, v.y};
+    }
   } else if constexpr (P == P32) {
-    float2 v = __ldg(p);
-    return {v.x, v.y};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(p + k * Vp));
+      u[2 * k] = {v.x, v.y};
+      u[2 * k + 1] = {v.z, v.w};
+    }
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p + 4 * Vp));
+    u[8] = {v.x, v.y};
   } else {
-    uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(p));
-    float2 f = h2f(u, P == PB16);
-    return {f.x, f.y};
+    constexpr bool BF = (P == PB16);
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+      const uint4 v = __ldg(p + k * Vp);
+      float2 a = h2f(v.x, BF), b = h2f(v.y, BF), c = h2f(v.z, BF), d = h2f(v.w, BF);
+      u[4 * k] = {a.x, a.y};
+      u[4 * k + 1] = {b.x, b.y};
+      u[4 * k + 2] = {c.x, c.y};
+      u[4 * k + 3] = {d.x, d.y};
+    }
+    const float2 a = h2f(__ldg(reinterpret_cast<const unsigned int*>(p + 2 * Vp)), BF);
+    u[8] = {a.x, a.y};
   }
 }
 
@@ -225,6 +249,8 @@ __device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
     h[0][a] = {p0.x + sgn * b0.x, p0.y + sgn * b0.y};
     h[1][a] = {p1.x + sgn * b1.x, p1.y + sgn * b1.y};
   }
+  cx<A> u[9];
+  load_link9<P>(u, links, Vp, site, dir);
   cx<A> g[2][3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -232,9 +258,8 @@ __device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
     g[1][a] = {A(0), A(0)};
 #pragma unroll
     for (int b = 0; b < 3; b++) {
-      const cx<A> u = load_link<P>(links, Vp, site, dir, a * 3 + b);
-      cfma(g[0][a], u, h[0][b]);
-      cfma(g[1][a], u, h[1][b]);
+      cfma(g[0][a], u[a * 3 + b], h[0][b]);
+      cfma(g[1][a], u[a * 3 + b], h[1][b]);
     }
   }
 #pragma unroll
@@ -288,8 +313,8 @@ struct RedArgs {
   double* rho;          // [nseg]
   double* alpha;        // [nseg]
   double* beta;         // [nseg]
-  const double* stop2;  // stop threshold on v (segment 0 only), nullable
-  int* conv;            // set to 1 when v <= *stop2, nullable
+  const double* stop2;  // per-segment stop threshold on v, nullable
+  int* conv;            // conv[seg] set to 1 when v <= stop2[seg], nullable
   const double* extra;  // FIN_ALPHA2: partial sum from a previous launch
   double* hist;         // FIN_BETA: hist[*hist_idx] = v (nullable)
   const int* hist_idx;
@@ -338,41 +363,61 @@ __device__ void finalize_value(const RedArgs& r, int seg, const double (&v)[NV])
     const double rho = r.rho[seg];
     r.beta[seg] = (rho > 0.0 && isfinite(x)) ? x / rho : 0.0;
     r.rho[seg] = x;
-    if (r.stop2 && r.conv && (x <= *r.stop2 || !isfinite(x))) *r.conv = 1;
+    if (r.stop2 && r.conv && (x <= r.stop2[seg] || !isfinite(x))) r.conv[seg] = 1;
     if (r.hist && *r.hist_idx < r.hist_cap) r.hist[*r.hist_idx] = x;
   }
 }
 
-// Called by every thread of the CTA after its per-thread values are known.
+// Called by every thread of the CTA after its per-thread values are known, for the 32-site
+// tile `tile` of segment `seg` whose tiles are [first, first + ntiles).  The last tile of the
+// segment to arrive sums the segment's partials in a fixed order (deterministic) and
+// finalizes.  Returns normally in every thread (usable inside a persistent tile loop).
 template <int NV>
-__device__ void grid_reduce(const RedArgs& r, double (&v)[NV], double* scratch) {
+__device__ void grid_reduce_seg(const RedArgs& r, double (&v)[NV], double* scratch, long tile,
+                                int seg, long first, int ntiles) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
   block_sum<NV>(v, scratch);
   __shared__ unsigned is_last;
-  const int seg = blockIdx.x / r.cps;
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; i++) r.partial[(long)blockIdx.x * NV + i] = v[i];
+    for (int i = 0; i < NV; i++) r.partial[tile * NV + i] = v[i];
     __threadfence();
     const unsigned prev = atomicAdd(&r.counter[seg], 1u);
-    is_last = (prev == (unsigned)r.cps - 1u);
+    is_last = (prev == (unsigned)ntiles - 1u);
   }
   __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  double s[NV];
+  if (is_last) {
+    __threadfence();
+    double s[NV];
 #pragma unroll
-  for (int i = 0; i < NV; i++) s[i] = 0.0;
-  const long base = (long)seg * r.cps;
-  for (int k = tid; k < r.cps; k += nthr)
+    for (int i = 0; i < NV; i++) s[i] = 0.0;
+    for (int k = tid; k < ntiles; k += nthr)
 #pragma unroll
-    for (int i = 0; i < NV; i++) s[i] += __ldcg(&r.partial[(base + k) * NV + i]);
-  block_sum<NV>(s, scratch);
-  if (tid == 0) {
-    finalize_value<NV>(r, seg, s);
-    r.counter[seg] = 0u;
+      for (int i = 0; i < NV; i++) s[i] += __ldcg(&r.partial[(first + k) * NV + i]);
+    block_sum<NV>(s, scratch);
+    if (tid == 0) {
+      finalize_value<NV>(r, seg, s);
+      r.counter[seg] = 0u;
+    }
   }
+  __syncthreads();
 }
+
+// Uniform segments of r.cps tiles (tile = blockIdx.x).
+template <int NV>
+__device__ void grid_reduce(const RedArgs& r, double (&v)[NV], double* scratch) {
+  const int seg = blockIdx.x / r.cps;
+  grid_reduce_seg<NV>(r, v, scratch, blockIdx.x, seg, (long)seg * r.cps, r.cps);
+}
+
+// Per-problem description of a batched (concatenated) site space: problem = segment.
+struct BatchSeg {
+  const void* mat[3];   // D+ M5op^-1, M5op^-dag D+^dag, D+^dag in the accumulation type
+  double l_alpha, l_beta, mf, db, dc;
+  int Vh;               // sites of one parity of this problem
+  int first_tile;       // first 32-site tile of the problem in the concatenation
+  int ntiles;
+};
 
 }  // namespace dwf

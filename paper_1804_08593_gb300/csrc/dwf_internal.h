@@ -61,6 +61,8 @@ struct Halo {
   uint32_t* nbr_he = nullptr;  // [8][He_tot] even halo -> odd (in block | HALO | FACE absent)
   int* ls_ho = nullptr;        // [Ho_tot] odd halo site -> its odd index (links)
   int* ls_he = nullptr;        // [He_tot] even halo site -> its even index (links)
+  void* links_ho[4] = {};      // per precision: links of the odd halo sites, contiguous
+  void* links_he[4] = {};      // per precision: links of the even halo sites, contiguous
   ~Halo();
 };
 
@@ -85,6 +87,10 @@ struct Matrices {
   void* d_m5idpt[2] = {};  // M5op^-dag D+^dag (post of stage A^dag)
   void* d_dpt[2] = {};     // D+^dag (post of stage B^dag and of D^dag)
   void* d_dp[2] = {};      // D+ (pre-op)
+  // FP16 16x16 tensor-core operands (core-matrix layout, [2 chiralities]) of
+  // {D+ M5op^-1, M5op^-dag D+^dag, D+^dag}
+  void* d_post_h[3] = {};
+  bool use_tc = true;
   double m5_alpha = 0, m5_beta = 0;  // M5op = alpha + beta K
   bool dplus_trivial = true;         // c == 0 (D+ = b)
 };
@@ -169,6 +175,7 @@ struct dwf_ctx {
   double* scal = nullptr;   // device scalars (see Scalars in solvers)
   size_t scal_len = 0;
   double* h_pinned = nullptr;  // pinned host mirror for scalar reads
+  int* dev_err = nullptr;      // set by a bounded device wait that gave up
   dwf::Profiler prof;
 };
 
@@ -179,6 +186,11 @@ dwf_status get_layout(dwf_ctx* h, const int block[4], Layout** out);
 dwf_status ensure_links(dwf_ctx* h, Layout* lay, int prec);
 dwf_status ensure_halo(dwf_ctx* h, Layout* lay);
 dwf_status build_matrices(dwf_ctx* h);
+// Host copies ([2][Ls][Ls] each, double) of D+ M5op^-1 (times b when c = 0, absorbing the
+// pre-op), M5op^-dag D+^dag and D+^dag, and M5op = alpha + beta K.
+bool fifth_dim_matrices(int Ls, double M5, double mf, double b, double c,
+                        std::vector<double>& dpm5i, std::vector<double>& m5idpt,
+                        std::vector<double>& dpt, double* alpha, double* beta);
 
 // Field sizes in bytes.
 inline size_t real_bytes(int prec) { return prec == P64 ? 8 : prec == P32 ? 4 : 2; }
@@ -222,6 +234,8 @@ struct VecArgs {
   int* stop_out;        // set *stop_out = *conv_in in the finalize (nullable)
   const int* conv_in;
   int* iter;            // incremented in the finalize (nullable)
+  const int* tile_seg;  // batched mode (nullable): per-problem stop/iter/scalars and D+
+  const BatchSeg* segp;
 };
 cudaError_t launch_vec(int prec, const VecArgs& a, int Ls, cudaStream_t st);
 
@@ -239,6 +253,8 @@ struct CastArgs {
   void* out2;            // nullable: second copy of out
   const int* stop;
   RedArgs red;
+  const int* tile_seg;   // batched mode (nullable)
+  const BatchSeg* segp;
 };
 cudaError_t launch_cast(int pin, int pout, const CastArgs& a, int Ls, cudaStream_t st);
 
@@ -262,6 +278,8 @@ struct VopArgs {
   const double* ap;
   const int* stop;
   RedArgs red;
+  const int* tile_seg;   // batched mode (nullable)
+  const BatchSeg* segp;
 };
 cudaError_t launch_vop(int prec, int prec_x, const VopArgs& a, int Ls, cudaStream_t st);
 
@@ -271,6 +289,7 @@ RedArgs make_red(dwf_ctx* h, int cps, int op, double* res);
 dwf_status stage_buffer(dwf_ctx* h, const char* name, const void* user, size_t bytes,
                         bool copy_in, void** dev);
 dwf_status finish_output(dwf_ctx* h, void* user, const void* dev, size_t bytes);
+dwf_status check_device_error(dwf_ctx* h);
 bool is_device_ptr(const void* p);
 
 }  // namespace dwf

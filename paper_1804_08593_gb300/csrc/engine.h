@@ -58,6 +58,19 @@ struct OpEngine {
   }
   RedArgs red(int op, double* res) const { return make_red(h, seg_cps, op, res); }
   int cls() const { return prec == P64 ? 0 : 1; }
+  // FP32/FP64 stages apply D+ M5op^-1 and M5op^-dag D+^dag by O(Ls) recurrences
+  void set_struct(StageArgs& a) const {
+    if (prec == P64 || prec == P32) {
+      a.post_struct = 1;
+      a.dp_b = h->b;
+      a.dp_c = h->c;
+      a.post_pre = trivial() ? h->b : 1.0;
+    }
+  }
+  // FP16 tensor-core operand of post matrix w (0: D+ M5op^-1, 1: M5op^-dag D+^dag, 2: D+^dag)
+  const void* post_h(int w) const {
+    return ((prec == P16 || prec == PB16) && h->mats.use_tc) ? h->mats.d_post_h[w] : nullptr;
+  }
   bool trivial() const { return h->mats.dplus_trivial; }
   const Geom& g() const { return lay->g; }
 
@@ -76,6 +89,7 @@ struct OpEngine {
     a.l_alpha = h->mats.m5_alpha;
     a.l_beta = h->mats.m5_beta;
     a.seg_cps = seg_cps;
+    a.err = h->dev_err;
     return a;
   }
   dwf_status launch(const StageArgs& a, bool dag) const {
@@ -85,7 +99,7 @@ struct OpEngine {
     const double sites = (double)(a.Vp / a.Vhb_pad) * a.Vhb;
     const double per_ss = 24.0 * R * (2.0 + (a.local_mode != LOC_NONE) + (a.epi == EPI_CG_R));
     const double bytes = sites * h->Ls * per_ss + sites * 8 * 18 * R;
-    const char* kind = a.link_site ? "halo" : (blocked ? "blocked" : "full");
+    const char* kind = a.Vp != lay->g.Vp ? "halo" : (blocked ? "blocked" : "full");
     char name[48];
     snprintf(name, sizeof(name), "hop_%s_%s%s", prec_name(prec), kind, a.post ? "_m5" : "");
     ProfScope ps(&h->prof, h->stream, name, bytes, 1320.0 * sites * h->Ls);
@@ -124,6 +138,8 @@ struct OpEngine {
     a.in = xin;
     a.out = t;
     a.post = h->mats.d_dpm5i[cls()];
+    a.post_h = post_h(0);
+    set_struct(a);
     a.epi = EPI_STORE;
     a.stop = stop;
     DWF_TRY(launch(a, false));
@@ -146,6 +162,8 @@ struct OpEngine {
     a.in = y;
     a.out = sb;
     a.post = h->mats.d_m5idpt[cls()];
+    a.post_h = post_h(1);
+    set_struct(a);
     a.epi = EPI_STORE;
     a.stop = stop;
     DWF_TRY(launch(a, true));
@@ -159,6 +177,9 @@ struct OpEngine {
     } else {
       b.hop_scale = -0.25;
       b.post = h->mats.d_dpt[cls()];
+      b.post_sparse = 1;
+      b.dp_b = h->b;
+      b.dp_c = h->c;
     }
     b.epi = epi;
     b.r = r;
@@ -182,7 +203,8 @@ struct OpEngine {
     a.Vhb = odd_halo ? H.Ho_b : H.He_b;
     a.Vhb_pad = odd_halo ? H.Ho_pad : H.He_pad;
     a.seg_cps = a.Vhb_pad / 32;
-    a.link_site = odd_halo ? H.ls_ho : H.ls_he;
+    a.links = odd_halo ? H.links_ho[prec] : H.links_he[prec];
+    a.Vp_link = a.Vp;
     return a;
   }
 
@@ -198,6 +220,7 @@ struct OpEngine {
     a.in = xin;
     a.skip_halo = 1;
     a.post = X;
+    a.post_h = post_h(0);
     a.out = B.t_int;
     a.stop = stop;
     DWF_TRY(launch(a, false));
@@ -205,6 +228,7 @@ struct OpEngine {
     b.in = xin;
     b.skip_halo = 1;
     b.post = X;
+    b.post_h = post_h(0);
     b.out = B.t_halo;
     b.stop = stop;
     DWF_TRY(launch(b, false));
@@ -247,6 +271,7 @@ struct OpEngine {
     a.in_halo = B.y_halo;
     a.Vp_halo = H.He_tot;
     a.post = Xd;
+    a.post_h = post_h(1);
     a.out = B.s_int;
     a.stop = stop;
     DWF_TRY(launch(a, true));
@@ -255,6 +280,7 @@ struct OpEngine {
     b.in_halo = B.y_halo;
     b.Vp_halo = H.He_tot;
     b.post = Xd;
+    b.post_h = post_h(1);
     b.out = B.s_halo;
     b.stop = stop;
     DWF_TRY(launch(b, true));
@@ -270,6 +296,9 @@ struct OpEngine {
     } else {
       c.hop_scale = -0.25;
       c.post = h->mats.d_dpt[cls()];
+      c.post_sparse = 1;
+      c.dp_b = h->b;
+      c.dp_c = h->c;
     }
     c.epi = EPI_CG_R;
     c.r = r;
@@ -307,6 +336,9 @@ struct OpEngine {
         } else {
           a.hop_scale = -0.5;
           a.post = h->mats.d_dpt[cls()];
+          a.post_sparse = 1;
+          a.dp_b = h->b;
+          a.dp_c = h->c;
         }
       }
       DWF_TRY(launch(a, dag));

@@ -1,6 +1,8 @@
 // Site orderings, neighbour tables, link packing and caller <-> internal field conversion.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <unordered_map>
 
 #include "dwf_internal.h"
 
@@ -132,6 +134,10 @@ Halo::~Halo() {
   cudaFree(nbr_he);
   cudaFree(ls_ho);
   cudaFree(ls_he);
+  for (int p = 0; p < 4; p++) {
+    cudaFree(links_ho[p]);
+    cudaFree(links_he[p]);
+  }
 }
 
 static long lex_of(const Geom& g, const int c[4]) {
@@ -212,22 +218,52 @@ dwf_status ensure_halo(dwf_ctx* h, Layout* lay) {
   H->He_pad = std::max(32, (H->He_b + 31) / 32 * 32);
   H->Ho_tot = (long)nb * H->Ho_pad;
   H->He_tot = (long)nb * H->He_pad;
-  auto pos = [](const std::vector<long>& v, long x) -> long {
-    auto it = std::lower_bound(v.begin(), v.end(), x);
-    return (it != v.end() && *it == x) ? (long)(it - v.begin()) : -1;
-  };
+  // Order each block's halo lists by the set of neighbours that exist (an 8-bit mask), so a
+  // warp's 32 halo sites take the same hop directions (no divergence over absent hops).
+  {
+    auto in_set = [](const std::vector<long>& v, long x) {
+      return std::binary_search(v.begin(), v.end(), x);
+    };
+    for (int b = 0; b < nb; b++) {
+      for (int odd = 0; odd < 2; odd++) {
+        std::vector<long>& L = odd ? ho[b] : he[b];
+        const std::vector<long>& other = odd ? he[b] : ho[b];
+        std::vector<std::pair<int, long>> keyed;
+        keyed.reserve(L.size());
+        for (long lx : L) {
+          int c[4], mask = 0;
+          coords_lex(g, lx, c);
+          for (int d = 0; d < 8; d++) {
+            int n[4];
+            neighbour(g, c, d, n);
+            if (blk_of(n) == b || in_set(other, lex_of(g, n))) mask |= 1 << d;
+          }
+          keyed.push_back({mask, lx});
+        }
+        std::sort(keyed.begin(), keyed.end());
+        for (size_t k = 0; k < keyed.size(); k++) L[k] = keyed[k].second;
+      }
+    }
+  }
+  // position of a site in a (reordered) halo list
+  std::vector<std::unordered_map<long, long>> hpos_o(nb), hpos_e(nb);
+  for (int b = 0; b < nb; b++) {
+    for (size_t k = 0; k < ho[b].size(); k++) hpos_o[b][ho[b][k]] = (long)k;
+    for (size_t k = 0; k < he[b].size(); k++) hpos_e[b][he[b][k]] = (long)k;
+  }
   std::vector<uint32_t> be(8 * (size_t)g.Vp, NBR_FACE), bo(8 * (size_t)g.Vp, NBR_FACE);
   std::vector<uint32_t> nho(8 * (size_t)H->Ho_tot, NBR_FACE), nhe(8 * (size_t)H->He_tot, NBR_FACE);
   std::vector<int> lho(H->Ho_tot, 0), lhe(H->He_tot, 0);
   // entry for a neighbour n of a site of block b: in block -> its index in the other
   // parity; in the halo list `hl` -> NBR_HALO | b * hpad + position; else absent.
-  auto entry = [&](int b, const int n[4], const std::vector<long>& hl, int hpad) -> uint32_t {
+  auto entry = [&](int b, const int n[4], bool to_odd_halo, int hpad) -> uint32_t {
     int nbk;
     const long nidx = index_of(g, n, &nbk);
     if (nbk == b) return (uint32_t)nidx;
-    const long q = pos(hl, lex_of(g, n));
-    if (q < 0) return NBR_FACE;
-    return NBR_HALO | (uint32_t)((long)b * hpad + q);
+    const auto& m = to_odd_halo ? hpos_o[b] : hpos_e[b];
+    const auto it = m.find(lex_of(g, n));
+    if (it == m.end()) return NBR_FACE;
+    return NBR_HALO | (uint32_t)((long)b * hpad + it->second);
   };
   for (int b = 0; b < nb; b++) {
     for (long j = 0; j < g.Vhb; j++) {
@@ -237,13 +273,13 @@ dwf_status ensure_halo(dwf_ctx* h, Layout* lay) {
       for (int d = 0; d < 8; d++) {
         int n[4];
         neighbour(g, c, d, n);
-        be[d * g.Vp + idx] = entry(b, n, ho[b], H->Ho_pad);
+        be[d * g.Vp + idx] = entry(b, n, true, H->Ho_pad);
       }
       coords_of(g, 1, idx, c);
       for (int d = 0; d < 8; d++) {
         int n[4];
         neighbour(g, c, d, n);
-        bo[d * g.Vp + idx] = entry(b, n, he[b], H->He_pad);
+        bo[d * g.Vp + idx] = entry(b, n, false, H->He_pad);
       }
     }
     for (size_t k = 0; k < ho[b].size(); k++) {
@@ -254,7 +290,7 @@ dwf_status ensure_halo(dwf_ctx* h, Layout* lay) {
       for (int d = 0; d < 8; d++) {
         int n[4];
         neighbour(g, c, d, n);
-        nho[d * H->Ho_tot + i] = entry(b, n, he[b], H->He_pad);
+        nho[d * H->Ho_tot + i] = entry(b, n, false, H->He_pad);
       }
     }
     for (size_t k = 0; k < he[b].size(); k++) {
@@ -265,7 +301,7 @@ dwf_status ensure_halo(dwf_ctx* h, Layout* lay) {
       for (int d = 0; d < 8; d++) {
         int n[4];
         neighbour(g, c, d, n);
-        nhe[d * H->He_tot + i] = entry(b, n, ho[b], H->Ho_pad);
+        nhe[d * H->He_tot + i] = entry(b, n, true, H->Ho_pad);
       }
     }
   }
@@ -276,22 +312,44 @@ dwf_status ensure_halo(dwf_ctx* h, Layout* lay) {
   DWF_TRY(upload_vec(lho, &H->ls_ho));
   DWF_TRY(upload_vec(lhe, &H->ls_he));
   lay->halo = std::move(H);
+  // links packed before the halo existed: repack so the halo copies get gathered
+  for (int p = 0; p < 4; p++) lay->links_valid[p] = false;
   return DWF_OK;
 }
 
 // ---------------------------------------------------------------------------------------
 // Links.
 // ---------------------------------------------------------------------------------------
+// Writes the 9 complex elements v[k] = (re, im) of one link as 16-byte chunks.
 template <int P>
-__device__ __forceinline__ typename Prec<P>::link2 to_link2(double re, double im) {
-  if constexpr (P == P64) return make_double2(re, im);
-  else if constexpr (P == P32) return make_float2((float)re, (float)im);
-  else if constexpr (P == P16) return __floats2half2_rn((float)re, (float)im);
-  else return __floats2bfloat162_rn((float)re, (float)im);
+__device__ __forceinline__ void store_link9(void* out, long Vp, long idx, int d,
+                                            const double (&re)[9], const double (&im)[9]) {
+  constexpr int NCHL = Prec<P>::NCHL;
+  uint4* o = reinterpret_cast<uint4*>(out) + (long)d * NCHL * Vp + idx;
+  if constexpr (P == P64) {
+    for (int k = 0; k < 9; k++) *reinterpret_cast<double2*>(o + k * Vp) = make_double2(re[k], im[k]);
+  } else if constexpr (P == P32) {
+    for (int k = 0; k < 5; k++) {
+      const int a = 2 * k, b = 2 * k + 1;
+      *reinterpret_cast<float4*>(o + k * Vp) =
+          make_float4((float)re[a], (float)im[a], b < 9 ? (float)re[b] : 0.f,
+                      b < 9 ? (float)im[b] : 0.f);
+    }
+  } else {
+    constexpr bool BF = (P == PB16);
+    for (int k = 0; k < 3; k++) {
+      uint32_t w[4];
+      for (int j = 0; j < 4; j++) {
+        const int e = 4 * k + j;
+        w[j] = e < 9 ? f2h((float)re[e], (float)im[e], BF) : 0u;
+      }
+      o[k * Vp] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
 }
 
 template <int P>
-__global__ void pack_links_kernel(const double2* __restrict__ U, typename Prec<P>::link2* out,
+__global__ void pack_links_kernel(const double2* __restrict__ U, void* out,
                                   const uint32_t* __restrict__ nbr, const int* __restrict__ lexp,
                                   const int* __restrict__ lexq, long Vp) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -299,52 +357,82 @@ __global__ void pack_links_kernel(const double2* __restrict__ U, typename Prec<P
   if (idx >= Vp) return;
   const int mu = d >> 1, back = d & 1;
   const int lx = lexp[idx];
+  double re[9], im[9];
   if (lx < 0) {
-    for (int k = 0; k < 9; k++) out[(long)(d * 9 + k) * Vp + idx] = to_link2<P>(0.0, 0.0);
-    return;
-  }
-  if (!back) {
+    for (int k = 0; k < 9; k++) re[k] = im[k] = 0.0;
+  } else if (!back) {
     const double2* u = U + ((long)lx * 4 + mu) * 9;
-    for (int k = 0; k < 9; k++) out[(long)(d * 9 + k) * Vp + idx] = to_link2<P>(u[k].x, u[k].y);
+    for (int k = 0; k < 9; k++) {
+      re[k] = u[k].x;
+      im[k] = u[k].y;
+    }
   } else {
     const int nl = lexq[nbr[(long)d * Vp + idx] & NBR_IDX];
     const double2* u = U + ((long)nl * 4 + mu) * 9;
     for (int a = 0; a < 3; a++)
-      for (int b = 0; b < 3; b++)
-        out[(long)(d * 9 + a * 3 + b) * Vp + idx] = to_link2<P>(u[b * 3 + a].x, -u[b * 3 + a].y);
+      for (int b = 0; b < 3; b++) {
+        re[a * 3 + b] = u[b * 3 + a].x;
+        im[a * 3 + b] = -u[b * 3 + a].y;
+      }
   }
+  store_link9<P>(out, Vp, idx, d, re, im);
+}
+
+// Copies the links of the sites listed in `site` ([n]) into a contiguous [8][NCHL][n] array.
+template <int P>
+__global__ void gather_links_kernel(const uint4* __restrict__ src, long Vp, uint4* dst, long n,
+                                    const int* __restrict__ site) {
+  constexpr int NCHL = Prec<P>::NCHL;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int d = blockIdx.y;
+  if (i >= n) return;
+  const long g = site[i];
+  for (int k = 0; k < NCHL; k++)
+    dst[((long)d * NCHL + k) * n + i] = src[((long)d * NCHL + k) * Vp + g];
+}
+
+static size_t link_bytes(int prec, long Vp) {
+  const int nchl = prec == P64 ? 9 : prec == P32 ? 5 : 3;
+  return (size_t)8 * nchl * 16 * (size_t)Vp;
 }
 
 dwf_status ensure_links(dwf_ctx* h, Layout* lay, int prec) {
   if (lay->links_valid[prec]) return DWF_OK;
   const Geom& g = lay->g;
-  const size_t elem = prec == P64 ? 16 : prec == P32 ? 8 : 4;
   for (int p = 0; p < 2; p++) {
     if (!lay->links[prec][p]) {
-      cudaError_t e = cudaMalloc(&lay->links[prec][p], elem * 8 * 9 * (size_t)g.Vp);
+      cudaError_t e = cudaMalloc(&lay->links[prec][p], link_bytes(prec, g.Vp));
       if (e != cudaSuccess) return set_error(DWF_ERR_NOMEM, "links allocation failed");
     }
     dim3 grid((unsigned)((g.Vp + 127) / 128), 8), block(128);
     const double2* U = reinterpret_cast<const double2*>(h->links_c128);
+    void* out = lay->links[prec][p];
     switch (prec) {
-      case P64:
-        pack_links_kernel<P64><<<grid, block, 0, h->stream>>>(
-            U, (double2*)lay->links[prec][p], lay->nbr[p], lay->lex[p], lay->lex[1 - p], g.Vp);
-        break;
-      case P32:
-        pack_links_kernel<P32><<<grid, block, 0, h->stream>>>(
-            U, (float2*)lay->links[prec][p], lay->nbr[p], lay->lex[p], lay->lex[1 - p], g.Vp);
-        break;
-      case P16:
-        pack_links_kernel<P16><<<grid, block, 0, h->stream>>>(
-            U, (__half2*)lay->links[prec][p], lay->nbr[p], lay->lex[p], lay->lex[1 - p], g.Vp);
-        break;
-      default:
-        pack_links_kernel<PB16><<<grid, block, 0, h->stream>>>(
-            U, (__nv_bfloat162*)lay->links[prec][p], lay->nbr[p], lay->lex[p], lay->lex[1 - p],
-            g.Vp);
+      case P64: pack_links_kernel<P64><<<grid, block, 0, h->stream>>>(U, out, lay->nbr[p], lay->lex[p], lay->lex[1 - p], g.Vp); break;
+      case P32: pack_links_kernel<P32><<<grid, block, 0, h->stream>>>(U, out, lay->nbr[p], lay->lex[p], lay->lex[1 - p], g.Vp); break;
+      case P16: pack_links_kernel<P16><<<grid, block, 0, h->stream>>>(U, out, lay->nbr[p], lay->lex[p], lay->lex[1 - p], g.Vp); break;
+      default: pack_links_kernel<PB16><<<grid, block, 0, h->stream>>>(U, out, lay->nbr[p], lay->lex[p], lay->lex[1 - p], g.Vp);
     }
     DWF_CUDA(cudaGetLastError());
+  }
+  // the block halos keep their own contiguous copies of the links of their sites
+  if (lay->halo) {
+    Halo& H = *lay->halo;
+    for (int odd = 0; odd < 2; odd++) {
+      const long n = odd ? H.Ho_tot : H.He_tot;
+      void*& dst = odd ? H.links_ho[prec] : H.links_he[prec];
+      if (!dst) DWF_CUDA(cudaMalloc(&dst, link_bytes(prec, n)));
+      dim3 grid((unsigned)((n + 127) / 128), 8), block(128);
+      const uint4* src = reinterpret_cast<const uint4*>(lay->links[prec][odd]);
+      const int* site = odd ? H.ls_ho : H.ls_he;
+      switch (prec) {
+        case P64: gather_links_kernel<P64><<<grid, block, 0, h->stream>>>(src, g.Vp, (uint4*)dst, n, site); break;
+        case P32: gather_links_kernel<P32><<<grid, block, 0, h->stream>>>(src, g.Vp, (uint4*)dst, n, site); break;
+        case P16: gather_links_kernel<P16><<<grid, block, 0, h->stream>>>(src, g.Vp, (uint4*)dst, n, site); break;
+        default: gather_links_kernel<PB16><<<grid, block, 0, h->stream>>>(src, g.Vp, (uint4*)dst, n, site);
+      }
+      DWF_CUDA(cudaGetLastError());
+    }
   }
   lay->links_valid[prec] = true;
   return DWF_OK;
@@ -554,7 +642,62 @@ dwf_status build_matrices(dwf_ctx* h) {
   DWF_TRY(upload(dpt, M.d_dpt));
   DWF_TRY(upload(dpm5i, M.d_dpm5i));
   DWF_TRY(upload(m5idpt, M.d_m5idpt));
+  // tensor-core operands: B[k][n] = M[n][k] stored K-major (row n, column k) in 8x8 core
+  // matrices, zero padded to 16 x 16, FP16
+  const std::vector<double>* src[3] = {&dpm5i, &m5idpt, &dpt};
+  for (int w = 0; w < 3; w++) {
+    std::vector<__half> hb(2 * 256, __float2half(0.f));
+    for (int chi = 0; chi < 2; chi++)
+      for (int n = 0; n < Ls; n++)
+        for (int k = 0; k < Ls; k++) {
+          const int off = (n / 8) * 128 + (k / 8) * 64 + (n % 8) * 8 + (k % 8);
+          hb[chi * 256 + off] = __float2half((float)(*src[w])[(chi * Ls + n) * Ls + k]);
+        }
+    if (!M.d_post_h[w]) DWF_CUDA(cudaMalloc(&M.d_post_h[w], hb.size() * sizeof(__half)));
+    DWF_CUDA(cudaMemcpy(M.d_post_h[w], hb.data(), hb.size() * sizeof(__half),
+                        cudaMemcpyHostToDevice));
+  }
+  const char* e = getenv("DWF_DISABLE_TC");
+  M.use_tc = !(e && e[0] == '1');
   return DWF_OK;
+}
+
+}  // namespace dwf
+
+// ---------------------------------------------------------------------------------------
+// Host helpers shared by the solvers.
+// ---------------------------------------------------------------------------------------
+namespace dwf {
+
+// The three post matrices of the stage kernels ([2][Ls][Ls] each, double): D+ M5op^-1
+// (times b when c = 0), M5op^-dag D+^dag and D+^dag, plus M5op = alpha + beta K.
+bool fifth_dim_matrices(int Ls, double M5, double mf, double b, double c,
+                        std::vector<double>& dpm5i, std::vector<double>& m5idpt,
+                        std::vector<double>& dpt, double* alpha, double* beta) {
+  const double a = (4.0 - M5) * b + 1.0, be = (4.0 - M5) * c - 1.0;
+  *alpha = a;
+  *beta = be;
+  dpm5i.clear();
+  m5idpt.clear();
+  dpt.clear();
+  for (int chi = 0; chi < 2; chi++) {
+    std::vector<double> K = kmat(Ls, mf, chi), D(Ls * Ls), M5m(Ls * Ls), M5i;
+    for (int i = 0; i < Ls * Ls; i++) {
+      const double id = (i % (Ls + 1) == 0) ? 1.0 : 0.0;
+      D[i] = b * id + c * K[i];
+      M5m[i] = a * id + be * K[i];
+    }
+    if (!invert(M5m, Ls, M5i)) return false;
+    std::vector<double> DM = matmul(D, M5i, Ls);
+    if (c == 0.0)
+      for (auto& v : DM) v *= b;
+    std::vector<double> MDt = matmul(transpose(M5i, Ls), transpose(D, Ls), Ls);
+    std::vector<double> Dt = transpose(D, Ls);
+    dpm5i.insert(dpm5i.end(), DM.begin(), DM.end());
+    m5idpt.insert(m5idpt.end(), MDt.begin(), MDt.end());
+    dpt.insert(dpt.end(), Dt.begin(), Dt.end());
+  }
+  return true;
 }
 
 }  // namespace dwf

@@ -450,15 +450,16 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, int l, int inner, int middl
   Timer timer;
   stats_init(stats);
   const Geom& g = lay->g;
+  long max_ctas = g.Vp / 32;
+  if (exact) {
+    // before the engines pack links: packing also gathers the halo copies
+    DWF_TRY(ensure_halo(h, lay));
+    max_ctas = std::max(max_ctas, lay->halo->He_tot / 32);
+  }
   OpEngine E64, Em, Ei;
   DWF_TRY(E64.init(h, lay, P64, false));
   DWF_TRY(Em.init(h, lay, middle, false));
   DWF_TRY(Ei.init(h, lay, inner, true));
-  long max_ctas = g.Vp / 32;
-  if (exact) {
-    DWF_TRY(ensure_halo(h, lay));
-    max_ctas = std::max(max_ctas, lay->halo->He_tot / 32);
-  }
   DWF_TRY(ensure_reduction(h, max_ctas * 2 + 64, g.nblocks + 64));
   const size_t f64 = field_bytes(g, P64), fm = field_bytes(g, middle), fi = field_bytes(g, inner);
   void *b64, *x64, *r64, *t1, *t2, *t3;

@@ -18,6 +18,7 @@
 #pragma once
 
 #include "dwf_device.cuh"
+#include "tc_m5.cuh"
 
 namespace dwf {
 
@@ -37,6 +38,13 @@ struct StageArgs {
   const void* links;     // links of parity p: [8][9][Vp]
   const uint32_t* nbr;   // neighbours of parity p: [8][Vp]
   const void* post;      // [2][Ls][Ls] in the accumulation type, nullable
+  const void* post_h;    // FP16/BF16 kernels: the same matrices as FP16 16x16 tensor-core
+                         // operands (core-matrix layout); nullable = CUDA-core path
+  int* err;              // set to 1 if a bounded device wait gives up (nullable)
+  int post_sparse;       // the post matrix is D+^dag = dp_b + dp_c K^dag: apply it sparsely
+  int post_struct;       // FP32/FP64: apply D+ M5op^-1 (M5op^-dag D+^dag when dag) by recurrences
+  double dp_b, dp_c;
+  double post_pre;       // extra factor of the structured post (b when the pre-op D+ = b)
   long Vp;               // site stride of out / in2 / r and of the neighbour table
   int Vhb, Vhb_pad;
   double hop_scale;
@@ -45,51 +53,333 @@ struct StageArgs {
   int epi;
   const double* alpha;   // EPI_CG_R: per-segment alpha
   int seg_cps;           // CTAs per scalar/reduction segment (Vp/32: one global segment)
-  const int* stop;       // nullable: skip everything when *stop != 0
+  const int* stop;       // nullable: skip everything when *stop != 0 (per segment if batched)
   RedArgs red;
+  // batched mode (nullable): tile -> problem map and per-problem parameters; the problem's
+  // post matrix is segp[seg].mat[post_which] when post is set
+  const int* tile_seg;
+  const BatchSeg* segp;
+  int post_which;
+  long ntiles;           // 32-site tiles (0: Vp / 32)
+  int grid;              // CTAs of a persistent launch (0: one CTA per tile)
 };
+
+// 16-bit storage: the neighbour's spinor and the link stay packed in registers (12 + 12
+// 32-bit words) and each element is converted to FP32 where it is used, which keeps the
+// kernel's register footprint low enough for more resident CTAs per SM.
+template <int P, int MU>
+__device__ __forceinline__ void hop_term16(Spinor<float>& acc, const uint4 (&q)[3],
+                                           const uint4* lp, long Vl, float sgn) {
+  constexpr bool BF = (P == PB16);
+  const uint4 l0 = __ldg(lp), l1 = __ldg(lp + Vl), l2 = __ldg(lp + 2 * Vl);
+  auto sp = [&](int k) -> cx<float> {
+    const uint4& w = q[k >> 2];
+    const uint32_t v = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
+    const float2 f = h2f(v, BF);
+    return {f.x, f.y};
+  };
+  auto lk = [&](int k) -> cx<float> {
+    const uint4& w = k < 4 ? l0 : (k < 8 ? l1 : l2);
+    const uint32_t v = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
+    const float2 f = h2f(v, BF);
+    return {f.x, f.y};
+  };
+  cx<float> h[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const cx<float> p0 = sp(a), p1 = sp(3 + a), p2 = sp(6 + a), p3 = sp(9 + a);
+    cx<float> b0, b1;
+    if constexpr (MU == 0) {
+      b0 = {p3.y, -p3.x};
+      b1 = {p2.y, -p2.x};
+    } else if constexpr (MU == 1) {
+      b0 = {-p3.x, -p3.y};
+      b1 = p2;
+    } else if constexpr (MU == 2) {
+      b0 = {p2.y, -p2.x};
+      b1 = {-p3.y, p3.x};
+    } else {
+      b0 = p2;
+      b1 = p3;
+    }
+    h[0][a] = {fmaf(sgn, b0.x, p0.x), fmaf(sgn, b0.y, p0.y)};
+    h[1][a] = {fmaf(sgn, b1.x, p1.x), fmaf(sgn, b1.y, p1.y)};
+  }
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    cx<float> g0 = {0.f, 0.f}, g1 = {0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      const cx<float> u = lk(a * 3 + b);
+      cfma(g0, u, h[0][b]);
+      cfma(g1, u, h[1][b]);
+    }
+    acc.c[a] = cadd(acc.c[a], g0);
+    acc.c[3 + a] = cadd(acc.c[3 + a], g1);
+    cx<float> l0, l1;   // B^dag g
+    if constexpr (MU == 0) {
+      l0 = {-g1.y, g1.x};
+      l1 = {-g0.y, g0.x};
+    } else if constexpr (MU == 1) {
+      l0 = g1;
+      l1 = {-g0.x, -g0.y};
+    } else if constexpr (MU == 2) {
+      l0 = {-g0.y, g0.x};
+      l1 = {g1.y, -g1.x};
+    } else {
+      l0 = g0;
+      l1 = g1;
+    }
+    acc.c[6 + a] = {fmaf(sgn, l0.x, acc.c[6 + a].x), fmaf(sgn, l0.y, acc.c[6 + a].y)};
+    acc.c[9 + a] = {fmaf(sgn, l1.x, acc.c[9 + a].x), fmaf(sgn, l1.y, acc.c[9 + a].y)};
+  }
+}
 
 template <int P, int D, bool DAG, bool BLOCKED>
 __device__ __forceinline__ void hop_dir(Spinor<typename Prec<P>::acc>& acc, const StageArgs& a,
                                         long site, long lsite, int s) {
   using A = typename Prec<P>::acc;
   const uint32_t nb = __ldg(a.nbr + (long)D * a.Vp + site);
-  Spinor<A> psi;
+  const void* src = a.in;
+  long vs = a.Vp_in;
   if constexpr (BLOCKED) {
     if (nb & NBR_FACE) return;
     if (nb & NBR_HALO) {
       if (a.skip_halo) return;
-      load_spinor<P>(psi, a.in_halo, a.Vp_halo, (long)(nb & NBR_IDX), s);
-    } else {
-      load_spinor<P>(psi, a.in, a.Vp_in, (long)(nb & NBR_IDX), s);
+      src = a.in_halo;
+      vs = a.Vp_halo;
     }
-  } else {
-    load_spinor<P>(psi, a.in, a.Vp_in, (long)(nb & NBR_IDX), s);
   }
+  const long j = (long)(nb & NBR_IDX);
   // forward hop: (1 - gamma_mu), backward: (1 + gamma_mu); the adjoint swaps them.
   constexpr bool back = (D & 1) != 0;
   const A sgn = (back != DAG) ? A(1) : A(-1);
-  hop_term<P, D / 2>(acc, psi, a.links, a.Vp_link, lsite, D, sgn);
+  if constexpr (P == P16 || P == PB16) {
+    const uint4* p = reinterpret_cast<const uint4*>(src) + ((long)s * 3) * vs + j;
+    const uint4 q[3] = {__ldg(p), __ldg(p + vs), __ldg(p + 2 * vs)};
+    const uint4* lp = reinterpret_cast<const uint4*>(a.links) + (long)D * 3 * a.Vp_link + lsite;
+    hop_term16<P, D / 2>(acc, q, lp, a.Vp_link, sgn);
+  } else {
+    Spinor<A> psi;
+    load_spinor<P>(psi, src, vs, j, s);
+    hop_term<P, D / 2>(acc, psi, a.links, a.Vp_link, lsite, D, sgn);
+  }
 }
 
-template <int P, int LS, bool DAG, bool BLOCKED>
-__global__ void __launch_bounds__(32 * LS) stage_kernel(const StageArgs a) {
-  using A = typename Prec<P>::acc;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red_scratch[32];
-  if (a.stop && *a.stop) return;
+// 16-bit stages: the eight neighbour spinors are gathered with cp.async into a per-thread
+// two-slot ring in shared memory, so the copy for direction d+1 is in flight while direction
+// d is computed (each thread reads back only what it copied: no block barrier needed).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::
+                   "r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
 
+// the 16-bit gather ring lives at the start of dynamic shared memory
+__host__ __device__ constexpr size_t ring_bytes16(int Ls) { return (size_t)2 * 3 * 32 * Ls * 16; }
+
+template <int P, bool DAG, bool BLOCKED>
+struct Hop16 {
+  const StageArgs& a;
+  long site, lsite;
+  int s, tid, nt;
+  uint4* ring;          // [2][3][nt] uint4
+  uint32_t nb[8];
+  __device__ __forceinline__ bool present(int d) const {
+    if constexpr (BLOCKED) {
+      if (nb[d] & NBR_FACE) return false;
+      if ((nb[d] & NBR_HALO) && a.skip_halo) return false;
+    }
+    return true;
+  }
+  __device__ __forceinline__ void issue(int d) {
+    if (present(d)) {
+      const void* src = a.in;
+      long vs = a.Vp_in;
+      if constexpr (BLOCKED) {
+        if (nb[d] & NBR_HALO) {
+          src = a.in_halo;
+          vs = a.Vp_halo;
+        }
+      }
+      const uint4* p = reinterpret_cast<const uint4*>(src) + ((long)s * 3) * vs + (nb[d] & NBR_IDX);
+      uint4* slot = ring + (d & 1) * 3 * nt + tid;
+#pragma unroll
+      for (int k = 0; k < 3; k++) cp_async16(slot + k * nt, p + k * vs);
+    }
+    cp_async_commit();
+  }
+  template <int D>
+  __device__ __forceinline__ void compute(Spinor<float>& acc) {
+    if (!present(D)) return;
+    const uint4* slot = ring + (D & 1) * 3 * nt + tid;
+    const uint4 q[3] = {slot[0], slot[nt], slot[2 * nt]};
+    constexpr bool back = (D & 1) != 0;
+    const float sgn = (back != DAG) ? 1.f : -1.f;
+    const uint4* lp = reinterpret_cast<const uint4*>(a.links) + (long)D * 3 * a.Vp_link + lsite;
+    hop_term16<P, D / 2>(acc, q, lp, a.Vp_link, sgn);
+  }
+  template <int D>
+  __device__ __forceinline__ void step(Spinor<float>& acc) {
+    if constexpr (D < 7) {
+      issue(D + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    compute<D>(acc);
+  }
+  __device__ __forceinline__ void run(Spinor<float>& acc) {
+#pragma unroll
+    for (int d = 0; d < 8; d++) nb[d] = __ldg(a.nbr + (long)d * a.Vp + site);
+    issue(0);
+    step<0>(acc);
+    step<1>(acc);
+    step<2>(acc);
+    step<3>(acc);
+    step<4>(acc);
+    step<5>(acc);
+    step<6>(acc);
+    step<7>(acc);
+  }
+};
+
+// Dense per-chirality Ls x Ls matrix along s on the tensor cores (FP16/BF16 kernels): the
+// CTA's 32 sites x 24 reals become A operands (rows = (real of one chirality, site), K = s'),
+// six tcgen05 MMAs (M=128, N=16, K=16) accumulate in tensor memory, and the results come back
+// through shared memory to the (site, s) threads.
+template <int LS>
+__device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const StageArgs& a,
+                                                 int lane, int s, int tid,
+                                                 unsigned char* smem, uint64_t* mbar,
+                                                 uint32_t* tslot) {
+  constexpr int NT = 32 * LS;
+  unsigned char* At = smem;
+  unsigned char* Bt = smem + 6 * tc::TILE_BYTES;
+  // the results are staged over the operand tiles: they are written only after every thread
+  // has seen the MMAs complete
+  float* Dst = reinterpret_cast<float*>(smem);
+  const uint4* bsrc = reinterpret_cast<const uint4*>(a.post_h);
+  for (int i = tid; i < 2 * tc::B_BYTES / 16; i += NT) reinterpret_cast<uint4*>(Bt)[i] = bsrc[i];
+  if constexpr (LS < 16) {
+    constexpr int PADK = 16 - LS;
+    for (int i = tid; i < 6 * 128 * PADK; i += NT) {
+      const int j = i / (128 * PADK), rem = i % (128 * PADK);
+      const int m = rem / PADK, k = LS + rem % PADK;
+      *reinterpret_cast<__half*>(At + j * tc::TILE_BYTES + tc::core_offset(m, k)) =
+          __float2half_rn(0.f);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 24; c++) {
+    const float v = (c & 1) ? acc.c[c >> 1].y : acc.c[c >> 1].x;
+    const int chi = c / 12, cp = c % 12;
+    const int f = cp * 32 + lane;
+    const int j = chi * 3 + (f >> 7), m = f & 127;
+    *reinterpret_cast<__half*>(At + j * tc::TILE_BYTES + tc::core_offset(m, s)) =
+        __float2half_rn(v);
+  }
+  if (s == 0) tc::tmem_alloc(tslot, tc::TMEM_COLS);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_f16(128, 16);
+#pragma unroll
+    for (int j = 0; j < 6; j++)
+      tc::mma_f16(taddr + 16u * j, tc::smem_desc(tc::smem_u32(At + j * tc::TILE_BYTES)),
+                  tc::smem_desc(tc::smem_u32(Bt + (j / 3) * tc::B_BYTES)), idesc, 0u);
+    tc::mma_commit(mbar);
+  }
+  if (!tc::mbar_wait(mbar, 0) && a.err) atomicExch(a.err, 1);
+  tc::fence_after_sync();
+  __syncthreads();
+  // warp s reads the TMEM lane quarter q = s % 4 (rows 32q..32q+31 = real cp%4 = q of every
+  // tile); the warps sharing a quarter split the six tiles between them
+  const int q = s & 3;
+  const int nq = (LS - q + 3) / 4;
+  for (int j = s >> 2; j < 6; j += nq) {
+    float v[16];
+    tc::tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + 16u * j, v);
+    const int chi = j / 3, cp = 4 * (j % 3) + q;
+    const int c = 12 * chi + cp;
+#pragma unroll
+    for (int n = 0; n < LS; n++) Dst[(n * 24 + c) * 32 + lane] = v[n];
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (s == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, tc::TMEM_COLS);
+  }
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    acc.c[k].x = Dst[(s * 24 + 2 * k) * 32 + lane];
+    acc.c[k].y = Dst[(s * 24 + 2 * k + 1) * 32 + lane];
+  }
+}
+
+// POST: 0 = no post matrix, 1 = CUDA-core column GEMM, 2 = tensor cores (16-bit only),
+//       3 = D+^dag applied sparsely (b + c K^dag: neighbours in s through shared memory),
+//       4 = D+ M5op^-1 (dag: M5op^-dag D+^dag) by an O(Ls) recurrence per column
+template <int P, int LS, bool DAG, bool BLOCKED, int POST>
+__device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
+                                           unsigned char* smem_raw, double* red_scratch,
+                                           uint64_t* tc_mbar, uint32_t* tc_slot) {
+  using A = typename Prec<P>::acc;
   const int lane = threadIdx.x, s = threadIdx.y;
   const int tid = lane + 32 * s;
   constexpr int NT = 32 * LS;
-  const long site = (long)blockIdx.x * 32 + lane;
-  const int cps = a.Vhb_pad >> 5;
-  const int jl = (blockIdx.x % cps) * 32 + lane;
-  const bool valid = jl < a.Vhb;
+  const long site = tile * 32 + lane;
+  int seg, ntl, jl, vh;
+  long first;
+  double l_alpha = a.l_alpha, l_beta = a.l_beta, mf = a.mf;
+  const void* post = a.post;
+  if (a.tile_seg) {
+    seg = __ldg(a.tile_seg + tile);
+    const BatchSeg& S = a.segp[seg];
+    if (a.stop && a.stop[seg]) return;
+    first = S.first_tile;
+    ntl = S.ntiles;
+    jl = (int)(tile - first) * 32 + lane;
+    vh = S.Vh;
+    l_alpha = S.l_alpha;
+    l_beta = S.l_beta;
+    mf = S.mf;
+    if (POST) post = S.mat[a.post_which];
+  } else {
+    if (a.stop && *a.stop) return;
+    const int cps = a.Vhb_pad >> 5;
+    seg = (int)(tile / a.seg_cps);
+    first = (long)seg * a.seg_cps;
+    ntl = a.seg_cps;
+    jl = (int)(tile % cps) * 32 + lane;
+    vh = a.Vhb;
+  }
+  const bool valid = jl < vh;
 
   Spinor<A> acc;
   zero(acc);
-  if (valid) {
+  if constexpr (P == P16 || P == PB16) {
+    if (valid) {
+      const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
+      Hop16<P, DAG, BLOCKED> hp{a, site, lsite, s, tid, NT,
+                                reinterpret_cast<uint4*>(smem_raw)};
+      hp.run(acc);
+    }
+    // the post stage reuses shared memory that other threads' rings occupy
+    __syncthreads();
+  } else if (valid) {
     const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
     hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
     hop_dir<P, 1, DAG, BLOCKED>(acc, a, site, lsite, s);
@@ -101,12 +391,123 @@ __global__ void __launch_bounds__(32 * LS) stage_kernel(const StageArgs a) {
     hop_dir<P, 7, DAG, BLOCKED>(acc, a, site, lsite, s);
   }
 
-  if (a.post != nullptr) {
+  if constexpr (POST == 2 && (P == P16 || P == PB16)) {
+    post_tensor_core<LS>(acc, a, lane, s, tid, smem_raw, tc_mbar, tc_slot);
+  }
+  if constexpr (POST == 3) {
+    // D+^dag h at s = b h_s + c (P+ h_{s+1} + P- h_{s-1}),  h_{Ls} = -mf h_0, h_{-1} = -mf h_{Ls-1}
+    double db = a.dp_b, dc = a.dp_c;
+    if (a.tile_seg) {
+      db = a.segp[seg].db;
+      dc = a.segp[seg].dc;
+    }
+    A* buf = reinterpret_cast<A*>(smem_raw);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      buf[(s * 24 + 2 * k) * 32 + lane] = acc.c[k].x;
+      buf[(s * 24 + 2 * k + 1) * 32 + lane] = acc.c[k].y;
+    }
+    __syncthreads();
+    const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
+    const A fu = (s + 1 < LS) ? A(1) : A(-mf), fd = (s > 0) ? A(1) : A(-mf);
+    const A b_ = A(db), c_ = A(dc);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const int sn = k < 6 ? su : sd;
+      const A f = k < 6 ? fu : fd;
+      acc.c[k].x = b_ * acc.c[k].x + c_ * f * buf[(sn * 24 + 2 * k) * 32 + lane];
+      acc.c[k].y = b_ * acc.c[k].y + c_ * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+    }
+  }
+  if constexpr (POST == 4) {
+    // Per chirality, K restricted to one chirality is a cyclic shift with a -mf corner:
+    // lower (y_{s-1}) for P+ without dag and P- with dag, upper (y_{s+1}) otherwise.
+    // M5op = alpha + beta K:  (I + r S) z = v with r = beta/alpha is solved by a one-sided
+    // recurrence w and the Sherman-Morrison correction for the corner:
+    //   lower: w_0 = v_0, w_s = v_s - r w_{s-1},  z_s = w_s + kappa (-r)^s w_{Ls-1},
+    //   upper: mirror image, kappa = r mf / (1 + mf (-r)^Ls);  M5op^-1 v = z / alpha.
+    double db = a.dp_b, dc = a.dp_c;
+    if (a.tile_seg) {
+      db = a.segp[seg].db;
+      dc = a.segp[seg].dc;
+    }
+    A* buf = reinterpret_cast<A*>(smem_raw);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      buf[(s * 24 + 2 * k) * 32 + lane] = acc.c[k].x;
+      buf[(s * 24 + 2 * k + 1) * 32 + lane] = acc.c[k].y;
+    }
+    __syncthreads();
+    const A r = A(l_beta / l_alpha), inva = A(1.0 / l_alpha);
+    A pw = A(1);
+    for (int i = 0; i < LS; i++) pw *= -r;
+    const A kappa = r * A(mf) / (A(1) + A(mf) * pw);
+    const A b_ = A(db), c_ = A(dc), mfA = A(mf), pre = A(a.post_pre);
+    for (int col = tid; col < 24 * 32; col += NT) {
+      const int c = col >> 5, l = col & 31;
+      const bool lower = ((c < 12) != DAG);
+      A v[LS];
+#pragma unroll
+      for (int t = 0; t < LS; t++) v[t] = buf[(t * 24 + c) * 32 + l];
+      if (DAG) {   // D+^dag first
+        A u[LS];
+#pragma unroll
+        for (int t = 0; t < LS; t++) {
+          const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
+                             : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
+          u[t] = b_ * v[t] + c_ * nb;
+        }
+#pragma unroll
+        for (int t = 0; t < LS; t++) v[t] = u[t];
+      }
+      if (lower) {
+#pragma unroll
+        for (int t = 1; t < LS; t++) v[t] = v[t] - r * v[t - 1];
+        const A e = kappa * v[LS - 1];
+        A g = A(1);
+#pragma unroll
+        for (int t = 0; t < LS; t++) {
+          v[t] = (v[t] + e * g) * inva;
+          g *= -r;
+        }
+      } else {
+#pragma unroll
+        for (int t = LS - 2; t >= 0; t--) v[t] = v[t] - r * v[t + 1];
+        const A e = kappa * v[0];
+        A g = A(1);
+#pragma unroll
+        for (int t = LS - 1; t >= 0; t--) {
+          v[t] = (v[t] + e * g) * inva;
+          g *= -r;
+        }
+      }
+      if (!DAG) {   // then D+ (times the absorbed pre-op factor)
+        A u[LS];
+#pragma unroll
+        for (int t = 0; t < LS; t++) {
+          const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
+                             : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
+          u[t] = pre * (b_ * v[t] + c_ * nb);
+        }
+#pragma unroll
+        for (int t = 0; t < LS; t++) v[t] = u[t];
+      }
+#pragma unroll
+      for (int t = 0; t < LS; t++) buf[(t * 24 + c) * 32 + l] = v[t];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      acc.c[k].x = buf[(s * 24 + 2 * k) * 32 + lane];
+      acc.c[k].y = buf[(s * 24 + 2 * k + 1) * 32 + lane];
+    }
+  }
+  if constexpr (POST == 1) {
     // Dense per-chirality Ls x Ls matrix along s: buf[s][24][32] holds the CTA's hop results;
     // each thread owns whole (component, site) columns and writes them back in place.
     A* buf = reinterpret_cast<A*>(smem_raw);
     A* mat = buf + LS * 24 * 32;
-    const A* pm = reinterpret_cast<const A*>(a.post);
+    const A* pm = reinterpret_cast<const A*>(post);
     for (int i = tid; i < 2 * LS * LS; i += NT) mat[i] = pm[i];
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -148,9 +549,9 @@ __global__ void __launch_bounds__(32 * LS) stage_kernel(const StageArgs a) {
     load_spinor<P>(x0, a.in2, a.Vp, site, s);
     load_spinor<P>(xu, a.in2, a.Vp, site, s + 1 < LS ? s + 1 : 0);
     load_spinor<P>(xd, a.in2, a.Vp, site, s > 0 ? s - 1 : LS - 1);
-    const A fu = (s + 1 < LS) ? A(1) : A(-a.mf);
-    const A fd = (s > 0) ? A(1) : A(-a.mf);
-    const A la = A(a.l_alpha), lb = A(a.l_beta);
+    const A fu = (s + 1 < LS) ? A(1) : A(-mf);
+    const A fd = (s > 0) ? A(1) : A(-mf);
+    const A la = A(l_alpha), lb = A(l_beta);
     const bool dagm = (a.local_mode == LOC_M5DAG);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -164,7 +565,7 @@ __global__ void __launch_bounds__(32 * LS) stage_kernel(const StageArgs a) {
 
   double nrm = 0.0;
   if (a.epi == EPI_CG_R) {
-    const A al = A(a.alpha[blockIdx.x / a.seg_cps]);
+    const A al = A(a.alpha[seg]);
     Spinor<A> rr;
     load_spinor<P>(rr, a.r, a.Vp, site, s);
 #pragma unroll
@@ -176,26 +577,50 @@ __global__ void __launch_bounds__(32 * LS) stage_kernel(const StageArgs a) {
     // the norm of what was stored (rounded to the storage precision)
     Spinor<A> back = rr;
     round_to_storage<P>(back);
+    A part = A(0);   // per-thread partial in the accumulation type; FP64 across threads
 #pragma unroll
-    for (int k = 0; k < 12; k++)
-      nrm += (double)back.c[k].x * back.c[k].x + (double)back.c[k].y * back.c[k].y;
+    for (int k = 0; k < 12; k++) part = fma(back.c[k].x, back.c[k].x, fma(back.c[k].y, back.c[k].y, part));
+    nrm = (double)part;
   } else {
     store_spinor<P>(a.out, a.Vp, site, s, acc);
     if (a.epi == EPI_NORM) {
+      A part = A(0);
 #pragma unroll
-      for (int k = 0; k < 12; k++)
-        nrm += (double)acc.c[k].x * acc.c[k].x + (double)acc.c[k].y * acc.c[k].y;
+      for (int k = 0; k < 12; k++) part = fma(acc.c[k].x, acc.c[k].x, fma(acc.c[k].y, acc.c[k].y, part));
+      nrm = (double)part;
     }
   }
   if (a.epi != EPI_STORE) {
     double v[1] = {nrm};
-    grid_reduce<1>(a.red, v, red_scratch);
+    grid_reduce_seg<1>(a.red, v, red_scratch, tile, seg, first, ntl);
+  }
+}
+
+// MINB = resident CTAs per SM the register budget is sized for (2 or 3); the launcher's
+// autotuner picks the faster one per kernel configuration.
+template <int P, int LS, bool DAG, bool BLOCKED, int POST, int MINB>
+__global__ void __launch_bounds__(32 * LS, MINB) stage_kernel(const StageArgs a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red_scratch[32];
+  __shared__ uint64_t tc_mbar;
+  __shared__ uint32_t tc_slot;
+  for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    stage_tile<P, LS, DAG, BLOCKED, POST>(a, tile, smem_raw, red_scratch, &tc_mbar, &tc_slot);
+    __syncthreads();
   }
 }
 
 template <int P>
-size_t stage_smem_bytes(int Ls, bool post) {
-  return post ? (size_t)(Ls * 24 * 32 + 2 * Ls * Ls) * sizeof(typename Prec<P>::acc) : 0;
+size_t stage_smem_bytes(int Ls, int post) {
+  const size_t ring = (P == P16 || P == PB16) ? ring_bytes16(Ls) : 0;
+  size_t need = 0;
+  if (post == 1) need = (size_t)(Ls * 24 * 32 + 2 * Ls * Ls) * sizeof(typename Prec<P>::acc);
+  if (post == 3 || post == 4) need = (size_t)Ls * 24 * 32 * sizeof(typename Prec<P>::acc);
+  if (post == 2) {
+    need = 6 * tc::TILE_BYTES + 2 * tc::B_BYTES;   // operands, then staged results
+    if ((size_t)Ls * 24 * 32 * 4 > need) need = (size_t)Ls * 24 * 32 * 4;
+  }
+  return need > ring ? need : ring;
 }
 
 }  // namespace dwf

@@ -228,7 +228,8 @@ def dwf_action(h: Handle, phi, X=None, tol=1e-12) -> float:
 
 
 def dwf_batch_solve(problems, tol, maxit, stream=None):
-    """problems: list of dicts with dims, Ls, M5, mf, b, c, links, phi, x (tensors/arrays)."""
+    """problems: list of dicts with dims, Ls, M5, mf, b, c, links, phi, x (tensors/arrays);
+    solves every A_i x_i = phi_i to tol and returns the per-problem statistics."""
     n = len(problems)
     arr = (Problem * n)()
     for i, p in enumerate(problems):
@@ -257,3 +258,4 @@ def dwf_profile_read(h: Handle) -> list:
     _check(load().dwf_profile_read(h.ptr, arr, cap, ctypes.byref(n)))
     return [dict(name=arr[i].name.decode(), launches=arr[i].launches, ms=arr[i].ms_total,
                  bytes=arr[i].bytes_total, flops=arr[i].flops_total) for i in range(n.value)]
+

@@ -117,3 +117,25 @@ def test_bad_arguments_raise():
     with pytest.raises(dwf.DWFError):
         dwf.dwf_mspcg(h, (3, 4, 4, 4), 2, "f32", "f32", x, cuda(np.zeros(x.shape, complex)),
                       1e-8, 10)                                          # bad block
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[3], CASES[4], CASES[5]])
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_tensor_core_m5_matches_cuda_core_path(case, prec, monkeypatch):
+    """The FP16/BF16 stages apply the Ls x Ls fifth-dimension matrices with tcgen05 MMAs;
+    DWF_DISABLE_TC=1 at handle creation selects the FP32 CUDA-core column GEMM instead.
+    Both must meet the 16-bit operator tolerance against the oracle and agree closely."""
+    dwf = lib()
+    rng, U, p = _setup(case, 7)
+    x = rand_even(rng, p.dims, p.Ls)
+    ref = o.mdagm(U, x, p)
+    outs = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("DWF_DISABLE_TC", flag)
+        h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
+        out = cuda(np.zeros_like(x))
+        dwf.dwf_apply(h, "MdagM", cuda(x), out, prec)
+        outs[flag] = host(out)
+        assert rel(outs[flag], ref) <= TOL[prec], (flag, rel(outs[flag], ref))
+    # both round the result to the same 16-bit storage, so they agree to that precision
+    assert rel(outs["0"], outs["1"]) <= TOL[prec]
