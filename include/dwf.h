@@ -176,6 +176,27 @@ typedef struct {
 dwf_status dwf_profile_enable(dwf_t handle, int on);
 dwf_status dwf_profile_read(dwf_t handle, dwf_kernel_profile* out, int capacity, int* n);
 
+/* Size of the device array that dwf_mdagm_noalloc works in: 64 MiB per GPU, held for the
+ * life of the process by every GPU that loads the library. */
+#define DWF_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* A = Mpc^dag Mpc on an even-half field for callers that cannot allocate device memory when
+ * they need the operator (a runtime that owns a fixed device budget, or code that must not
+ * call cudaMalloc/cudaFree mid-run).  The paper has no counterpart: this entry point exists
+ * for such callers only.  It creates no handle and calls no cudaMalloc, cudaFree or other
+ * allocating routine: the links (complex128 [T][Z][Y][X][4][3][3]), in and out (complex128
+ * [Ls][V/2][4][3]) are caller DEVICE buffers, and every intermediate (neighbour tables, packed
+ * links, fifth-dimension matrices, packed and intermediate fields) lives in one static device
+ * array of DWF_NOALLOC_SCRATCH_BYTES.  Lattices that need more return DWF_ERR_ARG with the
+ * required size in dwf_last_error() (FP64 fits up to about 8^4 x Ls = 16, FP32 twice that).
+ * The work is queued on stream (cudaStream_t, NULL = legacy default) and the call returns
+ * without synchronising.  The first call on each device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress); make it before any stream capture.  All
+ * calls share the array and leave their data in it, so calls that overlap on the GPU race. */
+dwf_status dwf_mdagm_noalloc(const int dims[4], int Ls, double M5, double mf, double b,
+                             double c, const void* links, const void* in, void* out,
+                             dwf_prec prec, void* stream);
+
 /* Thread-local description of the last error (never NULL). */
 const char* dwf_last_error(void);
 

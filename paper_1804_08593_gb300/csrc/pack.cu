@@ -665,9 +665,48 @@ dwf_status build_matrices(dwf_ctx* h) {
 }  // namespace dwf
 
 // ---------------------------------------------------------------------------------------
-// Host helpers shared by the solvers.
+// Launchers on caller-provided memory (used by the allocation-free entry point).
 // ---------------------------------------------------------------------------------------
 namespace dwf {
+
+cudaError_t launch_pack_links_to(int prec, const void* U, void* out, const uint32_t* nbr,
+                                 const int* lexp, const int* lexq, long Vp, cudaStream_t st) {
+  dim3 grid((unsigned)((Vp + 127) / 128), 8), block(128);
+  const double2* u = reinterpret_cast<const double2*>(U);
+  switch (prec) {
+    case P64: pack_links_kernel<P64><<<grid, block, 0, st>>>(u, out, nbr, lexp, lexq, Vp); break;
+    case P32: pack_links_kernel<P32><<<grid, block, 0, st>>>(u, out, nbr, lexp, lexq, Vp); break;
+    case P16: pack_links_kernel<P16><<<grid, block, 0, st>>>(u, out, nbr, lexp, lexq, Vp); break;
+    default: pack_links_kernel<PB16><<<grid, block, 0, st>>>(u, out, nbr, lexp, lexq, Vp);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_field_to(int prec, const void* src, void* dst, const int* map, long Vp,
+                                 long nsrc, int Ls, cudaStream_t st) {
+  dim3 grid((unsigned)((Vp + 127) / 128), Ls), block(128);
+  const double2* s = reinterpret_cast<const double2*>(src);
+  switch (prec) {
+    case P64: pack_field_kernel<P64><<<grid, block, 0, st>>>(s, dst, map, Vp, nsrc, 1.0, 0); break;
+    case P32: pack_field_kernel<P32><<<grid, block, 0, st>>>(s, dst, map, Vp, nsrc, 1.0, 0); break;
+    case P16: pack_field_kernel<P16><<<grid, block, 0, st>>>(s, dst, map, Vp, nsrc, 1.0, 0); break;
+    default: pack_field_kernel<PB16><<<grid, block, 0, st>>>(s, dst, map, Vp, nsrc, 1.0, 0);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_field_to(int prec, const void* src, void* dst, const int* map, long Vp,
+                                   long ndst, int Ls, cudaStream_t st) {
+  dim3 grid((unsigned)((Vp + 127) / 128), Ls), block(128);
+  double2* d = reinterpret_cast<double2*>(dst);
+  switch (prec) {
+    case P64: unpack_field_kernel<P64><<<grid, block, 0, st>>>(src, d, map, Vp, ndst, 1.0, 0); break;
+    case P32: unpack_field_kernel<P32><<<grid, block, 0, st>>>(src, d, map, Vp, ndst, 1.0, 0); break;
+    case P16: unpack_field_kernel<P16><<<grid, block, 0, st>>>(src, d, map, Vp, ndst, 1.0, 0); break;
+    default: unpack_field_kernel<PB16><<<grid, block, 0, st>>>(src, d, map, Vp, ndst, 1.0, 0);
+  }
+  return cudaGetLastError();
+}
 
 // The three post matrices of the stage kernels ([2][Ls][Ls] each, double): D+ M5op^-1
 // (times b when c = 0), M5op^-dag D+^dag and D+^dag, plus M5op = alpha + beta K.

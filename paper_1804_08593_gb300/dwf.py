@@ -27,7 +27,7 @@ LOCAL_DROP, LOCAL_EXACT = 0, 1
 # Every symbol include/dwf.h declares.
 EXPORTS = ("dwf_create", "dwf_update_links", "dwf_apply", "dwf_cg", "dwf_mspcg", "dwf_force",
            "dwf_action", "dwf_batch_solve", "dwf_last_error", "dwf_destroy", "dwf_version",
-           "dwf_profile_enable", "dwf_profile_read")
+           "dwf_profile_enable", "dwf_profile_read", "dwf_mdagm_noalloc")
 
 
 class DWFError(RuntimeError):
@@ -88,10 +88,11 @@ def load() -> ctypes.CDLL:
     lib.dwf_version.restype = ctypes.c_char_p
     lib.dwf_destroy.argtypes = [vp]
     lib.dwf_profile_enable.argtypes = [vp, i]
+    lib.dwf_mdagm_noalloc.argtypes = [ctypes.POINTER(i), i, d, d, d, d, vp, vp, vp, i, vp]
     lib.dwf_profile_read.argtypes = [vp, ctypes.POINTER(KernelProfile), i, ctypes.POINTER(i)]
     for name in ("dwf_create", "dwf_update_links", "dwf_apply", "dwf_cg", "dwf_mspcg",
                  "dwf_force", "dwf_action", "dwf_batch_solve", "dwf_profile_enable",
-                 "dwf_profile_read"):
+                 "dwf_profile_read", "dwf_mdagm_noalloc"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -259,3 +260,12 @@ def dwf_profile_read(h: Handle) -> list:
     return [dict(name=arr[i].name.decode(), launches=arr[i].launches, ms=arr[i].ms_total,
                  bytes=arr[i].bytes_total, flops=arr[i].flops_total) for i in range(n.value)]
 
+
+def dwf_mdagm_noalloc(dims, Ls, M5, mf, b, c, links, inp, out, prec="f64", stream=None):
+    """A = Mpc^dag Mpc for callers that cannot allocate device memory: device buffers only,
+    all scratch in the library's static device array; queued on the stream, not synchronised."""
+    arr = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(load().dwf_mdagm_noalloc(arr, int(Ls), float(M5), float(mf), float(b), float(c),
+                                    _ptr(links), _ptr(inp), _ptr(out), _prec(prec),
+                                    _stream_ptr(stream)))
+    return out
