@@ -259,6 +259,66 @@ def mdagm(U: np.ndarray, xe: np.ndarray, p: DWFParams) -> np.ndarray:
     return mpc_dag(U, mpc(U, xe, p), p)
 
 
+def even_site_coords(dims) -> np.ndarray:
+    """(t, z, y, x) of the even sites, in the order of the even-half vectors."""
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y), np.arange(X),
+                             indexing="ij")
+    c = np.stack([t, z, y, x], -1).reshape(-1, 4)
+    return c[parity(dims).reshape(-1) == 0]
+
+
+def mpc_at_sites(U: np.ndarray, xe: np.ndarray, p: DWFParams, sites, dag: bool = False):
+    """(Mpc x) or (Mpc^dag x) at the even-half indices `sites`, evaluated site by site from the
+    same definitions as mpc / mpc_dag: for an even site e, the odd intermediate at each of its
+    eight neighbours o is built from the even neighbours of o, then the hop back to e.  For
+    checks on lattices too large for the whole-lattice functions.  Returns (Ls, n, 4, 3)."""
+    X, Y, Z, T = p.dims
+    ext = np.array([T, Z, Y, X])
+    half = -np.ones((T, Z, Y, X), dtype=np.int64)
+    ec = even_site_coords(p.dims)
+    half[tuple(ec.T)] = np.arange(len(ec))
+    dp, m5, m5i = dplus_matrices(p), m5op_matrices(p), m5op_inv_matrices(p)
+    if dag:
+        dp, m5, m5i = transpose_chi(dp), transpose_chi(m5), transpose_chi(m5i)
+    sgn = 1.0 if dag else -1.0
+
+    def step(c, mu, d):            # neighbour c + d mu_hat, periodic (c = (t, z, y, x))
+        n = np.array(c)
+        n[3 - mu] = (n[3 - mu] + d) % ext[3 - mu]
+        return tuple(n)
+
+    def hop_at(get, c):            # (Dh psi)(c) or (Dh^dag psi)(c), psi(c') = get(c')
+        out = np.zeros((p.Ls, 4, 3), dtype=complex)
+        for mu in range(4):
+            f, b = step(c, mu, +1), step(c, mu, -1)
+            fwd = np.einsum("ab,lsb->lsa", U[c][mu], get(f))
+            bwd = np.einsum("ab,lsb->lsa", dagger(U[b][mu]), get(b))
+            out += np.einsum("ab,lbc->lac", ID4 + sgn * GAMMA[mu], fwd)
+            out += np.einsum("ab,lbc->lac", ID4 - sgn * GAMMA[mu], bwd)
+        return out
+
+    x_at = lambda c: xe[:, half[c]]
+    inner = {}
+
+    def t_at(o):                   # the odd intermediate of the Schur complement at o
+        if o not in inner:
+            if not dag:            # D+ M5op^-1 Dh_oe D+ x
+                inner[o] = s_apply(dp, s_apply(m5i, hop_at(lambda e: s_apply(dp, x_at(e)), o)))
+            else:                  # M5op^-dag D+^dag Dh^dag_oe y
+                inner[o] = s_apply(m5i, s_apply(dp, hop_at(x_at, o)))
+        return inner[o]
+
+    out = []
+    for k in sites:
+        e = tuple(ec[k])
+        g = hop_at(t_at, e)
+        if dag:
+            g = s_apply(dp, g)     # D+^dag Dh^dag_eo (.)
+        out.append(s_apply(m5, x_at(e)) - 0.25 * g)
+    return np.stack(out, axis=1)
+
+
 def m_eo(U: np.ndarray, xo_full: np.ndarray, p: DWFParams) -> np.ndarray:
     """M_eo x_o = -1/2 Dh_eo D+ x_o, as a full-lattice field (even sites)."""
     return _mask(-0.5 * hop(U, s_apply(dplus_matrices(p), xo_full)), p.dims, 0)

@@ -17,6 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "lib", "libdwf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+STAGE_PRECS = (0, 1, 2, 3)          # FP64, FP32, FP16, BF16
+STAGE_LS = (4, 6, 8, 10, 12, 16)    # fifth-dimension extents with compiled stage kernels
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 
@@ -38,16 +40,29 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list | None = N
     """Compiles every csrc/*.cu and links lib/libdwf.so; returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    # stage_ls.cu is compiled once per (storage precision, Ls): its kernel variants dominate
+    # the build, and the split lets them compile in parallel
+    units = []
+    for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
+        if os.path.basename(src) == "stage_ls.cu":
+            for p in STAGE_PRECS:
+                for ls in STAGE_LS:
+                    units.append((src, [f"-DDWF_STAGE_P={p}", f"-DDWF_STAGE_LS={ls}"],
+                                  f"stage_p{p}_ls{ls}.o"))
+        else:
+            units.append((src, [], os.path.basename(src)[:-3] + ".o"))
+    # the longest units first
+    units.sort(key=lambda u: (not u[1], u[2]))
     hdr = _headers_mtime()
     cc = nvcc()
     extra = list(extra or [])
 
-    def one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    def one(unit) -> str:
+        src, defs, name = unit
+        obj = os.path.join(BUILD, name)
         if os.path.exists(obj) and os.path.getmtime(obj) > max(os.path.getmtime(src), hdr):
             return obj
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *defs, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,9 +72,9 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list | None = N
             print(r.stderr, flush=True)
         return obj
 
-    jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
+    jobs = jobs or min(len(units), max(2, os.cpu_count() or 2))
     with ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(one, srcs))
+        objs = list(ex.map(one, units))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -51,6 +51,7 @@ struct Group {
   unsigned* counter = nullptr; // [nseg]
   double* partial = nullptr;   // [ntiles]
   int grid = 0;                // autotuned persistent grid of the stage launches
+  int post_struct = 1;         // every problem has |beta/alpha| < 1: post by recurrences
   std::vector<void*> owned;
   ~Group() {
     for (void* p : owned) cudaFree(p);
@@ -218,7 +219,7 @@ dwf_status g_mpc(const Group& G, int prec, const void* x, void* u, void* t, void
   a.out = t;
   a.post = G.mats[0];   // non-null marks a post stage; the problem's matrix comes from segp
   a.post_which = 0;
-  a.post_struct = 1;
+  a.post_struct = G.post_struct;
   a.post_pre = 1.0;
   DWF_CUDA(launch_stage_prec(prec, a, G.Ls, false, false, st));
   StageArgs b = gbase(G, prec, 0, stop);
@@ -246,7 +247,7 @@ dwf_status g_mpcdag(const Group& G, int prec, const void* y, void* sb, void* z, 
   a.out = sb;
   a.post = G.mats[0];
   a.post_which = 1;
-  a.post_struct = 1;
+  a.post_struct = G.post_struct;
   a.post_pre = 1.0;
   DWF_CUDA(launch_stage_prec(prec, a, G.Ls, true, false, st));
   StageArgs b = gbase(G, prec, 0, stop);
@@ -303,7 +304,7 @@ dwf_status g_cg_step(const Group& G, cudaStream_t st) {
   a.out = v[4];
   a.post = G.mats[1];
   a.post_which = 0;
-  a.post_struct = 1;
+  a.post_struct = G.post_struct;
   a.post_pre = 1.0;
   DWF_CUDA(launch_stage_prec(P32, a, G.Ls, false, false, st));
   StageArgs b = gbase(G, P32, 0, stop);
@@ -471,11 +472,14 @@ dwf_status build_group(Batch& B, Group& G, const dwf_problem* pr) {
       for (int w = 0; w < 3; w++)
         S.mat[w] = pr2 ? (const void*)((float*)G.mats[1] + k * msz + w * 2 * Ls * Ls)
                        : (const void*)((double*)G.mats[0] + k * msz + w * 2 * Ls * Ls);
+      if (!(std::fabs(lb) < std::fabs(la))) G.post_struct = 0;
       S.l_alpha = la;
       S.l_beta = lb;
       S.mf = P.mf;
       S.db = P.b;
       S.dc = P.c;
+      S.k64 = make_coef5<double>(la, lb, P.mf, P.b, P.c, 1.0, Ls);
+      S.k32 = make_coef5<float>(la, lb, P.mf, P.b, P.c, 1.0, Ls);
       S.Vh = (int)P.Vh;
       S.first_tile = (int)P.first_tile;
       S.ntiles = (int)P.ntiles;

@@ -180,7 +180,15 @@ __global__ void cast_kernel(const CastArgs a) {
   __syncthreads();
   const AW f = AW(fsh);
   Spinor<AI> v;
-  load_spinor<PI>(v, a.in, a.Vp, site, s);
+  if (a.in_map) {   // a gather from another site order
+    const int j = a.in_map[site];
+    if (j >= 0)
+      load_spinor<PI>(v, a.in, a.Vp_in, j, s);
+    else
+      zero(v);
+  } else {
+    load_spinor<PI>(v, a.in, a.Vp, site, s);
+  }
   Spinor<AO> w;
 #pragma unroll
   for (int k = 0; k < 12; k++) w.c[k] = {AO((AW)v.c[k].x * f), AO((AW)v.c[k].y * f)};
@@ -346,16 +354,6 @@ cudaError_t launch_vop(int prec, int prec_x, const VopArgs& a, int Ls, cudaStrea
     case P32: return vop_px<P32>(prec_x, a, g, b, st);
     case P16: return vop_px<P16>(prec_x, a, g, b, st);
     default: return vop_px<PB16>(prec_x, a, g, b, st);
-  }
-}
-
-cudaError_t launch_stage_prec(int prec, const StageArgs& a, int Ls, bool dag, bool blocked,
-                              cudaStream_t st) {
-  switch (prec) {
-    case P64: return launch_stage<P64>(a, Ls, dag, blocked, st);
-    case P32: return launch_stage<P32>(a, Ls, dag, blocked, st);
-    case P16: return launch_stage<P16>(a, Ls, dag, blocked, st);
-    default: return launch_stage<PB16>(a, Ls, dag, blocked, st);
   }
 }
 

@@ -412,9 +412,30 @@ __device__ void grid_reduce(const RedArgs& r, double (&v)[NV], double* scratch) 
 }
 
 // Per-problem description of a batched (concatenated) site space: problem = segment.
+// Fifth-dimension coefficients of a stage in one arithmetic type, computed on the host so
+// that FP32 kernels run no FP64 instructions (GB300's FP64 pipe is narrow):
+// M5op = la + lb K with walls -mf, D+ = db + dc K, and for the recurrence post r = lb/la,
+// inva = 1/la, kappa = r mf / (1 + mf (-r)^Ls), pre = extra factor of D+ M5op^-1.
+template <typename A>
+struct Coef5 {
+  A la, lb, mf, db, dc, r, inva, kappa, pre;
+};
+template <typename A>
+inline Coef5<A> make_coef5(double la, double lb, double mf, double db, double dc, double pre,
+                           int Ls) {
+  const double r = la != 0.0 ? lb / la : 0.0;
+  double pw = 1.0;
+  for (int i = 0; i < Ls; i++) pw *= -r;
+  const double kappa = r * mf / (1.0 + mf * pw);
+  return {A(la), A(lb), A(mf), A(db), A(dc), A(r), A(la != 0.0 ? 1.0 / la : 0.0), A(kappa),
+          A(pre)};
+}
+
 struct BatchSeg {
   const void* mat[3];   // D+ M5op^-1, M5op^-dag D+^dag, D+^dag in the accumulation type
   double l_alpha, l_beta, mf, db, dc;
+  Coef5<double> k64;    // the same coefficients for the stage kernels (pre = 1)
+  Coef5<float> k32;
   int Vh;               // sites of one parity of this problem
   int first_tile;       // first 32-site tile of the problem in the concatenation
   int ntiles;

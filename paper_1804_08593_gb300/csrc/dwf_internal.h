@@ -73,6 +73,8 @@ struct Layout {
   uint32_t* nbr[2] = {nullptr, nullptr};   // [8][Vp] per output parity
   int* lex[2] = {nullptr, nullptr};        // internal index -> lexicographic site (-1 = pad)
   int* cb_even = nullptr;                  // internal even index -> caller even-half index
+  int* cb_inv = nullptr;                   // caller even-half index -> internal even index
+                                           // ([V/2 rounded up to 32], -1 = pad)
   void* links[4][2] = {};                  // [precision][parity] packed links, lazily built
   bool links_valid[4] = {false, false, false, false};
   ~Layout();
@@ -91,6 +93,11 @@ struct Matrices {
   // {D+ M5op^-1, M5op^-dag D+^dag, D+^dag}
   void* d_post_h[3] = {};
   bool use_tc = true;
+  // how the stages apply the dense fifth-dimension post matrices: 0 auto (recurrences for
+  // FP32/FP64, the faster of recurrences and tensor cores for FP16/BF16), 1 matrices only
+  // (tensor cores for FP16/BF16), 2 recurrences only; recurrences need |beta/alpha| < 1
+  int post_mode = 0;
+  bool struct_ok = false;
   double m5_alpha = 0, m5_beta = 0;  // M5op = alpha + beta K
   bool dplus_trivial = true;         // c == 0 (D+ = b)
 };
@@ -210,9 +217,9 @@ dwf_status pack_full(dwf_ctx* h, Layout* lay, const void* src_c128, void* dst_ev
 dwf_status unpack_full(dwf_ctx* h, Layout* lay, const void* src_even, const void* src_odd,
                        int prec, void* dst_c128);
 
-// ---- stage kernels (stage_f*.cu) ----
-template <int P>
-cudaError_t launch_stage(const StageArgs& a, int Ls, bool dag, bool blocked, cudaStream_t st);
+// ---- stage kernels (stage_ls.cu per precision and Ls, stage_dispatch.cu) ----
+template <int P, int LS>
+cudaError_t stage_dispatch_ls(const StageArgs& a, bool dag, bool blocked, cudaStream_t st);
 cudaError_t launch_stage_prec(int prec, const StageArgs& a, int Ls, bool dag, bool blocked,
                               cudaStream_t st);
 
@@ -245,6 +252,8 @@ struct CastArgs {
   const void* in;
   void* out;
   long Vp;
+  const int* in_map;     // nullable: out site i reads in site in_map[i] (-1: zero)
+  long Vp_in;            // site stride of in when in_map is set
   int Vhb, Vhb_pad;
   double num;
   const double* den;     // nullable

@@ -58,14 +58,14 @@ struct OpEngine {
   }
   RedArgs red(int op, double* res) const { return make_red(h, seg_cps, op, res); }
   int cls() const { return prec == P64 ? 0 : 1; }
-  // FP32/FP64 stages apply D+ M5op^-1 and M5op^-dag D+^dag by O(Ls) recurrences
+  // how a stage applies D+ M5op^-1 / M5op^-dag D+^dag (call after post_h is set)
   void set_struct(StageArgs& a) const {
-    if (prec == P64 || prec == P32) {
-      a.post_struct = 1;
-      a.dp_b = h->b;
-      a.dp_c = h->c;
-      a.post_pre = trivial() ? h->b : 1.0;
-    }
+    const Matrices& M = h->mats;
+    if (!M.struct_ok || M.post_mode == 1) return;
+    a.post_struct = (M.post_mode == 0 && a.post_h) ? 2 : 1;
+    a.dp_b = h->b;
+    a.dp_c = h->c;
+    a.post_pre = trivial() ? h->b : 1.0;
   }
   // FP16 tensor-core operand of post matrix w (0: D+ M5op^-1, 1: M5op^-dag D+^dag, 2: D+^dag)
   const void* post_h(int w) const {
@@ -97,11 +97,14 @@ struct OpEngine {
     // site and slice; the 8 links of each output site once
     const double R = (double)real_bytes(prec);
     const double sites = (double)(a.Vp / a.Vhb_pad) * a.Vhb;
-    const double per_ss = 24.0 * R * (2.0 + (a.local_mode != LOC_NONE) + (a.epi == EPI_CG_R));
+    const double per_ss = 24.0 * R * (2.0 + (a.local_mode != LOC_NONE) + (a.epi == EPI_CG_R) -
+                                      (a.epi == EPI_NORM_ONLY));
     const double bytes = sites * h->Ls * per_ss + sites * 8 * 18 * R;
     const char* kind = a.Vp != lay->g.Vp ? "halo" : (blocked ? "blocked" : "full");
     char name[48];
-    snprintf(name, sizeof(name), "hop_%s_%s%s", prec_name(prec), kind, a.post ? "_m5" : "");
+    // _m5: dense D+ M5op^-1 / M5op^-dag D+^dag post; _dp: sparse D+^dag post
+    snprintf(name, sizeof(name), "hop_%s_%s%s", prec_name(prec), kind,
+             a.post ? (a.post_sparse ? "_dp" : "_m5") : "");
     ProfScope ps(&h->prof, h->stream, name, bytes, 1320.0 * sites * h->Ls);
     DWF_CUDA(launch_stage_prec(prec, a, h->Ls, dag, blocked, h->stream));
     return DWF_OK;
@@ -210,8 +213,9 @@ struct OpEngine {
 
   // y = Mpc P_s p (u = D+ p unless D+ = b); per block: pap_int = ||y||^2 on the block, then
   // alpha = rho / (||y||^2 on the block + on the halo).
+  // store_y = false: only the norms are needed (no A^dag stage follows)
   dwf_status exact_mpc(const void* p, const void* u, const ExactBufs& B, double* pap_int,
-                       double* rho, double* alpha, const int* stop) const {
+                       double* rho, double* alpha, const int* stop, bool store_y = true) const {
     const Halo& H = *lay->halo;
     const void* xin = trivial() ? p : u;
     const void* X = h->mats.d_dpm5i[cls()];
@@ -221,6 +225,7 @@ struct OpEngine {
     a.skip_halo = 1;
     a.post = X;
     a.post_h = post_h(0);
+    set_struct(a);
     a.out = B.t_int;
     a.stop = stop;
     DWF_TRY(launch(a, false));
@@ -229,6 +234,7 @@ struct OpEngine {
     b.skip_halo = 1;
     b.post = X;
     b.post_h = post_h(0);
+    set_struct(b);
     b.out = B.t_halo;
     b.stop = stop;
     DWF_TRY(launch(b, false));
@@ -241,7 +247,7 @@ struct OpEngine {
     c.local_mode = LOC_M5;
     c.hop_scale = -0.25;
     c.out = B.y_int;
-    c.epi = EPI_NORM;
+    c.epi = store_y ? EPI_NORM : EPI_NORM_ONLY;
     c.red = red(FIN_STORE, pap_int);
     c.stop = stop;
     DWF_TRY(launch(c, false));
@@ -251,7 +257,7 @@ struct OpEngine {
     d.Vp_halo = H.Ho_tot;
     d.hop_scale = -0.25;
     d.out = B.y_halo;
-    d.epi = EPI_NORM;
+    d.epi = store_y ? EPI_NORM : EPI_NORM_ONLY;
     d.red = make_red(h, H.He_pad / 32, FIN_ALPHA2, nullptr);
     d.red.rho = rho;
     d.red.alpha = alpha;
@@ -272,6 +278,7 @@ struct OpEngine {
     a.Vp_halo = H.He_tot;
     a.post = Xd;
     a.post_h = post_h(1);
+    set_struct(a);
     a.out = B.s_int;
     a.stop = stop;
     DWF_TRY(launch(a, true));
@@ -281,6 +288,7 @@ struct OpEngine {
     b.Vp_halo = H.He_tot;
     b.post = Xd;
     b.post_h = post_h(1);
+    set_struct(b);
     b.out = B.s_halo;
     b.stop = stop;
     DWF_TRY(launch(b, true));

@@ -15,6 +15,7 @@ Layout::~Layout() {
     for (int q = 0; q < 4; q++) cudaFree(links[q][p]);
   }
   cudaFree(cb_even);
+  cudaFree(cb_inv);
 }
 
 // Coordinates (x, y, z, t) of internal site idx of parity p; false for padding.
@@ -118,6 +119,12 @@ dwf_status get_layout(dwf_ctx* h, const int block[4], Layout** out) {
   }
   DWF_CUDA(cudaMalloc(&lay->cb_even, cbe.size() * sizeof(int)));
   DWF_CUDA(cudaMemcpy(lay->cb_even, cbe.data(), cbe.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
+  std::vector<int> inv((g.V / 2 + 31) / 32 * 32, -1);
+  for (long idx = 0; idx < g.Vp; idx++)
+    if (cbe[idx] >= 0) inv[cbe[idx]] = (int)idx;
+  DWF_CUDA(cudaMalloc(&lay->cb_inv, inv.size() * sizeof(int)));
+  DWF_CUDA(cudaMemcpy(lay->cb_inv, inv.data(), inv.size() * sizeof(int),
                       cudaMemcpyHostToDevice));
   *out = lay.get();
   h->layouts.push_back(std::move(lay));
@@ -659,6 +666,10 @@ dwf_status build_matrices(dwf_ctx* h) {
   }
   const char* e = getenv("DWF_DISABLE_TC");
   M.use_tc = !(e && e[0] == '1');
+  const char* pm = getenv("DWF_POST");   // auto | matrix | recurrence
+  M.post_mode = !pm ? 0 : pm[0] == 'm' ? 1 : pm[0] == 'r' ? 2 : 0;
+  if (!M.use_tc && M.post_mode == 0) M.post_mode = 1;
+  M.struct_ok = std::fabs(be) < std::fabs(a);
   return DWF_OK;
 }
 

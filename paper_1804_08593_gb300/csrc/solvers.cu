@@ -47,12 +47,16 @@ static dwf_status vop(const OpEngine& E, int op, const void* x, void* y, RedArgs
   return DWF_OK;
 }
 
+// out (Eout's layout and precision) = f * in, f = num or sqrt(num / *den) (inverted if asked);
+// in_map: in is in another site order (out site i reads in site in_map[i], stride vp_in)
 static dwf_status cast(const OpEngine& Eout, int pin, const void* in, void* out, double num,
                        const double* den, int invert, const void* dotv, RedArgs red,
-                       void* out2 = nullptr) {
+                       void* out2 = nullptr, const int* in_map = nullptr, long vp_in = 0) {
   CastArgs a{};
   a.in = in;
   a.out = out;
+  a.in_map = in_map;
+  a.Vp_in = vp_in;
   a.Vp = Eout.g().Vp;
   a.Vhb = Eout.g().Vhb;
   a.Vhb_pad = Eout.g().Vhb_pad;
@@ -386,19 +390,26 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
   double* alpha_b = blk + nb;
   double* beta_b = blk + 2 * nb;
   double* pap_b = blk + 3 * nb;
+  // the outer vectors are in caller (lexicographic) site order, the local solves in block
+  // order: the casts between the two gather through the layout's index maps
+  const bool remap = (Em.lay != Ei.lay);
   DWF_TRY(cast(Ei, Em.prec, r, iv.ri, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 0,
-               nullptr, Ei.red(FIN_STORE, rho_b), iv.pi));
+               nullptr, Ei.red(FIN_STORE, rho_b), iv.pi, remap ? Ei.lay->cb_even : nullptr,
+               Em.g().Vp));
   DWF_TRY(vop(Ei, VOP_ZERO, nullptr, iv.xi));
   if (!Ei.trivial()) DWF_TRY(Ei.dplus(iv.pi, iv.ui, nullptr));
   double* papx_b = blk + 4 * nb;
   for (int k = 0; k < l; k++) {
+    // the last local iteration needs only ||Mpc p||^2 (for alpha), not Mpc p itself
+    const bool last = (k + 1 == l);
     if (iv.exact) {
-      DWF_TRY(Ei.exact_mpc(iv.pi, iv.ui, iv.eb, papx_b, rho_b, alpha_b, nullptr));
+      DWF_TRY(Ei.exact_mpc(iv.pi, iv.ui, iv.eb, papx_b, rho_b, alpha_b, nullptr, !last));
     } else {
       RedArgs ra = Ei.red(FIN_ALPHA, pap_b);
       ra.rho = rho_b;
       ra.alpha = alpha_b;
-      DWF_TRY(Ei.mpc(iv.pi, iv.ui, iv.ti, iv.yi, EPI_NORM, ra, nullptr, true));
+      DWF_TRY(Ei.mpc(iv.pi, iv.ui, iv.ti, iv.yi, last ? EPI_NORM_ONLY : EPI_NORM, ra, nullptr,
+                     true));
     }
     VecArgs va{};
     va.x = iv.xi;
@@ -433,10 +444,11 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
     rz.rho = dsc + S_RHO;
     rz.beta = dsc + S_BETA;
     DWF_TRY(cast(Em, Ei.prec, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
-                 r, rz));
+                 r, rz, nullptr, remap ? Ei.lay->cb_inv : nullptr, Ei.g().Vp));
   } else {
     DWF_TRY(cast(Em, Ei.prec, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
-                 r, Em.red(FIN_STORE, dsc + S_RZNEW)));
+                 r, Em.red(FIN_STORE, dsc + S_RZNEW), nullptr,
+                 remap ? Ei.lay->cb_inv : nullptr, Ei.g().Vp));
     DWF_TRY(vop(Em, VOP_DOT, rold, z, Em.red(FIN_STORE, dsc + S_TMP)));
     pr_beta_kernel<<<1, 1, 0, Em.h->stream>>>(dsc);
     DWF_CUDA(cudaGetLastError());
@@ -444,24 +456,27 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
   return DWF_OK;
 }
 
-static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, int l, int inner, int middle, bool flex,
-                            bool exact, const void* b_c128, void* x_c128, double tol, int maxit,
-                            dwf_stats* stats) {
+// lay: the block layout of the local solves; layL: the caller (lexicographic) order of the
+// outer iteration, whose hops stay local in memory (the block order scatters them)
+static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int inner,
+                            int middle, bool flex, bool exact, const void* b_c128, void* x_c128,
+                            double tol, int maxit, dwf_stats* stats) {
   Timer timer;
   stats_init(stats);
-  const Geom& g = lay->g;
-  long max_ctas = g.Vp / 32;
+  const Geom& g = layL->g;     // outer vectors
+  const Geom& gb = lay->g;     // local solves
+  long max_ctas = std::max(g.Vp, gb.Vp) / 32;
   if (exact) {
     // before the engines pack links: packing also gathers the halo copies
     DWF_TRY(ensure_halo(h, lay));
     max_ctas = std::max(max_ctas, lay->halo->He_tot / 32);
   }
   OpEngine E64, Em, Ei;
-  DWF_TRY(E64.init(h, lay, P64, false));
-  DWF_TRY(Em.init(h, lay, middle, false));
+  DWF_TRY(E64.init(h, layL, P64, false));
+  DWF_TRY(Em.init(h, layL, middle, false));
   DWF_TRY(Ei.init(h, lay, inner, true));
-  DWF_TRY(ensure_reduction(h, max_ctas * 2 + 64, g.nblocks + 64));
-  const size_t f64 = field_bytes(g, P64), fm = field_bytes(g, middle), fi = field_bytes(g, inner);
+  DWF_TRY(ensure_reduction(h, max_ctas * 2 + 64, gb.nblocks + 64));
+  const size_t f64 = field_bytes(g, P64), fm = field_bytes(g, middle), fi = field_bytes(gb, inner);
   void *b64, *x64, *r64, *t1, *t2, *t3;
   DWF_TRY(h->ws->get("ms_b64", f64, &b64));
   DWF_TRY(h->ws->get("ms_x64", f64, &x64));
@@ -500,16 +515,16 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, int l, int inner, int middl
   }
   double *dsc, *blk;
   DWF_TRY(h->ws->get("ms_scal", S_NSLOT * sizeof(double), (void**)&dsc));
-  DWF_TRY(h->ws->get("ms_blk", 5 * (size_t)g.nblocks * sizeof(double), (void**)&blk));
+  DWF_TRY(h->ws->get("ms_blk", 5 * (size_t)gb.nblocks * sizeof(double), (void**)&blk));
   DWF_CUDA(cudaMemsetAsync(dsc, 0, S_NSLOT * sizeof(double), h->stream));
 
-  DWF_TRY(pack_even(h, lay, b_c128, b64, P64, 1.0));
+  DWF_TRY(pack_even(h, layL, b_c128, b64, P64, 1.0));
   DWF_TRY(vop(E64, VOP_ZERO, nullptr, x64));
   double bb, rr64, rrm;
   DWF_TRY(true_residual(E64, b64, nullptr, r64, t1, t2, t3, dsc, &bb));
   if (!(bb > 0.0) || !std::isfinite(bb)) {
     if (bb == 0.0) {
-      DWF_TRY(unpack_even(h, lay, x64, P64, x_c128, 1.0));
+      DWF_TRY(unpack_even(h, layL, x64, P64, x_c128, 1.0));
       DWF_CUDA(cudaStreamSynchronize(h->stream));
       return DWF_OK;
     }
@@ -518,7 +533,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, int l, int inner, int middl
   rr64 = bb;
   const double tol2 = tol * tol * bb;
   const double delta = (middle == P64) ? 0.0 : 0.1;
-  const int nbk = g.nblocks;
+  const int nbk = gb.nblocks;
 
   DWF_TRY(cast(Em, P64, r64, rm, 1.0, nullptr, 0, nullptr, Em.red(FIN_STORE, dsc + S_RR)));
   DWF_TRY(vop(Em, VOP_ZERO, nullptr, xm));
@@ -596,7 +611,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, int l, int inner, int middl
     DWF_TRY(vop(E64, VOP_ADD_CAST, xm, x64, RedArgs{}, 1.0, nullptr, middle));
     DWF_TRY(true_residual(E64, b64, x64, r64, t1, t2, t3, dsc, &rr64));
   }
-  DWF_TRY(unpack_even(h, lay, x64, P64, x_c128, 1.0));
+  DWF_TRY(unpack_even(h, layL, x64, P64, x_c128, 1.0));
   DWF_CUDA(cudaStreamSynchronize(h->stream));
   if (stats) {
     stats->iterations = k;
@@ -629,11 +644,13 @@ extern "C" dwf_status dwf_mspcg(dwf_t h, const int block[4], int inner_iters, dw
     return set_error(DWF_ERR_ARG, "unknown local_op");
   Layout* lay;
   DWF_TRY(get_layout(h, block, &lay));
+  Layout* layL;
+  DWF_TRY(get_layout(h, h->dims, &layL));
   const size_t ub = (size_t)h->Ls * (lay->g.V / 2) * 12 * 16;
   void *db, *dx;
   DWF_TRY(stage_buffer(h, "io_phi", phi, ub, true, &db));
   DWF_TRY(stage_buffer(h, "io_x", x, ub, false, &dx));
-  dwf_status st = run_mspcg(h, lay, inner_iters, (int)inner, (int)middle, flexible != 0,
+  dwf_status st = run_mspcg(h, lay, layL, inner_iters, (int)inner, (int)middle, flexible != 0,
                             local_op == DWF_LOCAL_EXACT, db, dx, tol, maxit, stats);
   if (st != DWF_OK && st != DWF_ERR_NOT_CONVERGED) return st;
   dwf_status st2 = finish_output(h, x, dx, ub);

@@ -23,7 +23,8 @@
 namespace dwf {
 
 enum LocalMode { LOC_NONE = 0, LOC_M5 = 1, LOC_M5DAG = 2 };
-enum EpiMode { EPI_STORE = 0, EPI_NORM = 1, EPI_CG_R = 2 };
+// EPI_NORM_ONLY: the reduction of EPI_NORM without storing the output (its only use)
+enum EpiMode { EPI_STORE = 0, EPI_NORM = 1, EPI_CG_R = 2, EPI_NORM_ONLY = 3 };
 
 struct StageArgs {
   const void* in;        // hop input, parity 1-p
@@ -42,7 +43,8 @@ struct StageArgs {
                          // operands (core-matrix layout); nullable = CUDA-core path
   int* err;              // set to 1 if a bounded device wait gives up (nullable)
   int post_sparse;       // the post matrix is D+^dag = dp_b + dp_c K^dag: apply it sparsely
-  int post_struct;       // FP32/FP64: apply D+ M5op^-1 (M5op^-dag D+^dag when dag) by recurrences
+  int post_struct;       // dense post D+ M5op^-1 (dag: M5op^-dag D+^dag) by O(Ls) recurrences:
+                         // 0 no, 1 yes, 2 the faster of recurrences and tensor cores (16-bit)
   double dp_b, dp_c;
   double post_pre;       // extra factor of the structured post (b when the pre-op D+ = b)
   long Vp;               // site stride of out / in2 / r and of the neighbour table
@@ -50,6 +52,10 @@ struct StageArgs {
   double hop_scale;
   int local_mode;
   double l_alpha, l_beta, mf;
+  // filled from the fields above by finish_stage_args() at launch
+  float hs32;
+  Coef5<double> k64;
+  Coef5<float> k32;
   int epi;
   const double* alpha;   // EPI_CG_R: per-segment alpha
   int seg_cps;           // CTAs per scalar/reduction segment (Vp/32: one global segment)
@@ -63,6 +69,21 @@ struct StageArgs {
   long ntiles;           // 32-site tiles (0: Vp / 32)
   int grid;              // CTAs of a persistent launch (0: one CTA per tile)
 };
+
+template <typename A>
+__device__ __forceinline__ Coef5<A> coef5(const StageArgs& a) {
+  if constexpr (sizeof(A) == 8) return a.k64; else return a.k32;
+}
+template <typename A>
+__device__ __forceinline__ Coef5<A> coef5(const BatchSeg& S) {
+  if constexpr (sizeof(A) == 8) return S.k64; else return S.k32;
+}
+inline void finish_stage_args(StageArgs& a, int Ls) {
+  a.hs32 = (float)a.hop_scale;
+  const double pre = a.post_pre != 0.0 ? a.post_pre : 1.0;
+  a.k64 = make_coef5<double>(a.l_alpha, a.l_beta, a.mf, a.dp_b, a.dp_c, pre, Ls);
+  a.k32 = make_coef5<float>(a.l_alpha, a.l_beta, a.mf, a.dp_b, a.dp_c, pre, Ls);
+}
 
 // 16-bit storage: the neighbour's spinor and the link stay packed in registers (12 + 12
 // 32-bit words) and each element is converted to FP32 where it is used, which keeps the
@@ -135,21 +156,47 @@ __device__ __forceinline__ void hop_term16(Spinor<float>& acc, const uint4 (&q)[
   }
 }
 
-template <int P, int D, bool DAG, bool BLOCKED>
-__device__ __forceinline__ void hop_dir(Spinor<typename Prec<P>::acc>& acc, const StageArgs& a,
-                                        long site, long lsite, int s) {
-  using A = typename Prec<P>::acc;
-  const uint32_t nb = __ldg(a.nbr + (long)D * a.Vp + site);
-  const void* src = a.in;
-  long vs = a.Vp_in;
+// How a stage gathers the eight neighbour spinors (a launch-variant choice, timed by the
+// autotuner): straight into registers; through a two-slot cp.async ring in shared memory
+// (caching in L1, or in L2 only); or into registers with the indices loaded up front and
+// direction d+1 prefetched into L1 while direction d is computed.
+enum Gather { G_REG = 0, G_RING_CA = 1, G_PF = 2, G_RING_CG = 3 };
+
+// source array, site stride and presence of the neighbour behind table entry nb
+template <bool BLOCKED>
+__device__ __forceinline__ bool nbr_source(const StageArgs& a, uint32_t nb, const void*& src,
+                                           long& vs) {
+  src = a.in;
+  vs = a.Vp_in;
   if constexpr (BLOCKED) {
-    if (nb & NBR_FACE) return;
+    if (nb & NBR_FACE) return false;
     if (nb & NBR_HALO) {
-      if (a.skip_halo) return;
+      if (a.skip_halo) return false;
       src = a.in_halo;
       vs = a.Vp_halo;
     }
   }
+  return true;
+}
+
+template <int P, bool BLOCKED>
+__device__ __forceinline__ void prefetch_nbr(const StageArgs& a, uint32_t nb, int s) {
+  const void* src;
+  long vs;
+  if (!nbr_source<BLOCKED>(a, nb, src, vs)) return;
+  constexpr int NCH = Prec<P>::NCH;
+  const uint4* p = reinterpret_cast<const uint4*>(src) + ((long)s * NCH) * vs + (nb & NBR_IDX);
+#pragma unroll
+  for (int k = 0; k < NCH; k++) asm volatile("prefetch.global.L1 [%0];" :: "l"(p + k * vs));
+}
+
+template <int P, int D, bool DAG, bool BLOCKED>
+__device__ __forceinline__ void hop_dir_nb(Spinor<typename Prec<P>::acc>& acc,
+                                           const StageArgs& a, uint32_t nb, long lsite, int s) {
+  using A = typename Prec<P>::acc;
+  const void* src;
+  long vs;
+  if (!nbr_source<BLOCKED>(a, nb, src, vs)) return;
   const long j = (long)(nb & NBR_IDX);
   // forward hop: (1 - gamma_mu), backward: (1 + gamma_mu); the adjoint swaps them.
   constexpr bool back = (D & 1) != 0;
@@ -166,13 +213,26 @@ __device__ __forceinline__ void hop_dir(Spinor<typename Prec<P>::acc>& acc, cons
   }
 }
 
-// 16-bit stages: the eight neighbour spinors are gathered with cp.async into a per-thread
-// two-slot ring in shared memory, so the copy for direction d+1 is in flight while direction
-// d is computed (each thread reads back only what it copied: no block barrier needed).
+template <int P, int D, bool DAG, bool BLOCKED>
+__device__ __forceinline__ void hop_dir(Spinor<typename Prec<P>::acc>& acc, const StageArgs& a,
+                                        long site, long lsite, int s) {
+  hop_dir_nb<P, D, DAG, BLOCKED>(acc, a, __ldg(a.nbr + (long)D * a.Vp + site), lsite, s);
+}
+
+// FP32 and 16-bit stages: the eight neighbour spinors are gathered with cp.async into a
+// per-thread two-slot ring in shared memory, so the copy for direction d+1 is in flight while
+// direction d is computed (each thread reads back only what it copied: no block barrier
+// needed) and no registers are tied up by loads in flight.
+template <bool L1>
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::
-                   "r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))), "l"(gmem)
-               : "memory");
+  if constexpr (L1)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::
+                     "r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))), "l"(gmem)
+                 : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::
+                     "r"(static_cast<uint32_t>(__cvta_generic_to_shared(smem))), "l"(gmem)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;" ::: "memory");
@@ -182,15 +242,19 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
-// the 16-bit gather ring lives at the start of dynamic shared memory
-__host__ __device__ constexpr size_t ring_bytes16(int Ls) { return (size_t)2 * 3 * 32 * Ls * 16; }
+// the gather ring lives at the start of dynamic shared memory: [2][NCH][32 Ls] x 16 bytes
+template <int P>
+__host__ __device__ constexpr size_t ring_bytes(int Ls) {
+  return (P == P16 || P == PB16 || P == P32) ? (size_t)2 * Prec<P>::NCH * 32 * Ls * 16 : 0;
+}
 
-template <int P, bool DAG, bool BLOCKED>
-struct Hop16 {
+template <int P, bool DAG, bool BLOCKED, bool L1>
+struct HopRing {
+  static constexpr int NC = Prec<P>::NCH;
   const StageArgs& a;
   long site, lsite;
   int s, tid, nt;
-  uint4* ring;          // [2][3][nt] uint4
+  uint4* ring;          // [2][NC][nt] uint4
   uint32_t nb[8];
   __device__ __forceinline__ bool present(int d) const {
     if constexpr (BLOCKED) {
@@ -209,22 +273,34 @@ struct Hop16 {
           vs = a.Vp_halo;
         }
       }
-      const uint4* p = reinterpret_cast<const uint4*>(src) + ((long)s * 3) * vs + (nb[d] & NBR_IDX);
-      uint4* slot = ring + (d & 1) * 3 * nt + tid;
+      const uint4* p =
+          reinterpret_cast<const uint4*>(src) + ((long)s * NC) * vs + (nb[d] & NBR_IDX);
+      uint4* slot = ring + (d & 1) * NC * nt + tid;
 #pragma unroll
-      for (int k = 0; k < 3; k++) cp_async16(slot + k * nt, p + k * vs);
+      for (int k = 0; k < NC; k++) cp_async16<L1>(slot + k * nt, p + k * vs);
     }
     cp_async_commit();
   }
   template <int D>
   __device__ __forceinline__ void compute(Spinor<float>& acc) {
     if (!present(D)) return;
-    const uint4* slot = ring + (D & 1) * 3 * nt + tid;
-    const uint4 q[3] = {slot[0], slot[nt], slot[2 * nt]};
+    const uint4* slot = ring + (D & 1) * NC * nt + tid;
     constexpr bool back = (D & 1) != 0;
     const float sgn = (back != DAG) ? 1.f : -1.f;
-    const uint4* lp = reinterpret_cast<const uint4*>(a.links) + (long)D * 3 * a.Vp_link + lsite;
-    hop_term16<P, D / 2>(acc, q, lp, a.Vp_link, sgn);
+    if constexpr (P == P32) {
+      Spinor<float> psi;
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        const float4 v = *reinterpret_cast<const float4*>(slot + k * nt);
+        psi.c[2 * k] = {v.x, v.y};
+        psi.c[2 * k + 1] = {v.z, v.w};
+      }
+      hop_term<P, D / 2>(acc, psi, a.links, a.Vp_link, lsite, D, sgn);
+    } else {
+      const uint4 q[3] = {slot[0], slot[nt], slot[2 * nt]};
+      const uint4* lp = reinterpret_cast<const uint4*>(a.links) + (long)D * 3 * a.Vp_link + lsite;
+      hop_term16<P, D / 2>(acc, q, lp, a.Vp_link, sgn);
+    }
   }
   template <int D>
   __device__ __forceinline__ void step(Spinor<float>& acc) {
@@ -255,17 +331,20 @@ struct Hop16 {
 // CTA's 32 sites x 24 reals become A operands (rows = (real of one chirality, site), K = s'),
 // six tcgen05 MMAs (M=128, N=16, K=16) accumulate in tensor memory, and the results come back
 // through shared memory to the (site, s) threads.
+//
+// Shared memory of a tensor-core stage: [0, 3072 Ls) the 16-bit gather ring, reused for the
+// staged results (both are exactly 3072 Ls bytes); then the six A tiles and the two B
+// matrices.  The TMEM columns, the mbarrier, the B matrices and the zero K padding of the A
+// tiles are set up once per CTA (tc_setup) and kept for every tile the CTA processes.
+__host__ __device__ constexpr size_t tc_offset(int Ls) { return (size_t)3072 * Ls; }
+
 template <int LS>
-__device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const StageArgs& a,
-                                                 int lane, int s, int tid,
-                                                 unsigned char* smem, uint64_t* mbar,
-                                                 uint32_t* tslot) {
+__device__ __forceinline__ void tc_setup(const StageArgs& a, unsigned char* smem,
+                                         uint64_t* mbar, uint32_t* tslot) {
   constexpr int NT = 32 * LS;
-  unsigned char* At = smem;
-  unsigned char* Bt = smem + 6 * tc::TILE_BYTES;
-  // the results are staged over the operand tiles: they are written only after every thread
-  // has seen the MMAs complete
-  float* Dst = reinterpret_cast<float*>(smem);
+  const int tid = threadIdx.x + 32 * threadIdx.y;
+  unsigned char* At = smem + tc_offset(LS);
+  unsigned char* Bt = At + 6 * tc::TILE_BYTES;
   const uint4* bsrc = reinterpret_cast<const uint4*>(a.post_h);
   for (int i = tid; i < 2 * tc::B_BYTES / 16; i += NT) reinterpret_cast<uint4*>(Bt)[i] = bsrc[i];
   if constexpr (LS < 16) {
@@ -277,6 +356,28 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
           __float2half_rn(0.f);
     }
   }
+  if (threadIdx.y == 0) tc::tmem_alloc(tslot, tc::TMEM_COLS);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_proxy_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+}
+
+// after the tile loop's final barrier: every tcgen05.ld has completed
+__device__ __forceinline__ void tc_teardown(const uint32_t* tslot) {
+  tc::fence_after_sync();
+  if (threadIdx.y == 0) tc::tmem_dealloc(*tslot, tc::TMEM_COLS);
+}
+
+template <int LS>
+__device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const StageArgs& a,
+                                                 int lane, int s, int tid,
+                                                 unsigned char* smem, uint64_t* mbar,
+                                                 uint32_t* tslot, uint32_t& phase) {
+  unsigned char* At = smem + tc_offset(LS);
+  const unsigned char* Bt = At + 6 * tc::TILE_BYTES;
+  float* Dst = reinterpret_cast<float*>(smem);
 #pragma unroll
   for (int c = 0; c < 24; c++) {
     const float v = (c & 1) ? acc.c[c >> 1].y : acc.c[c >> 1].x;
@@ -286,8 +387,6 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
     *reinterpret_cast<__half*>(At + j * tc::TILE_BYTES + tc::core_offset(m, s)) =
         __float2half_rn(v);
   }
-  if (s == 0) tc::tmem_alloc(tslot, tc::TMEM_COLS);
-  if (tid == 0) tc::mbar_init(mbar, 1);
   tc::fence_proxy_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -301,11 +400,12 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
                   tc::smem_desc(tc::smem_u32(Bt + (j / 3) * tc::B_BYTES)), idesc, 0u);
     tc::mma_commit(mbar);
   }
-  if (!tc::mbar_wait(mbar, 0) && a.err) atomicExch(a.err, 1);
+  if (!tc::mbar_wait(mbar, phase) && a.err) atomicExch(a.err, 1);
+  phase ^= 1u;
   tc::fence_after_sync();
-  __syncthreads();
   // warp s reads the TMEM lane quarter q = s % 4 (rows 32q..32q+31 = real cp%4 = q of every
-  // tile); the warps sharing a quarter split the six tiles between them
+  // tile); the warps sharing a quarter split the six tiles between them.  The staging area is
+  // the gather ring, idle since the barrier after the hop.
   const int q = s & 3;
   const int nq = (LS - q + 3) / 4;
   for (int j = s >> 2; j < 6; j += nq) {
@@ -318,10 +418,6 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (s == 0) {
-    tc::fence_after_sync();
-    tc::tmem_dealloc(taddr, tc::TMEM_COLS);
-  }
 #pragma unroll
   for (int k = 0; k < 12; k++) {
     acc.c[k].x = Dst[(s * 24 + 2 * k) * 32 + lane];
@@ -332,10 +428,11 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
 // POST: 0 = no post matrix, 1 = CUDA-core column GEMM, 2 = tensor cores (16-bit only),
 //       3 = D+^dag applied sparsely (b + c K^dag: neighbours in s through shared memory),
 //       4 = D+ M5op^-1 (dag: M5op^-dag D+^dag) by an O(Ls) recurrence per column
-template <int P, int LS, bool DAG, bool BLOCKED, int POST>
+template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
                                            unsigned char* smem_raw, double* red_scratch,
-                                           uint64_t* tc_mbar, uint32_t* tc_slot) {
+                                           uint64_t* tc_mbar, uint32_t* tc_slot,
+                                           uint32_t& tc_phase) {
   using A = typename Prec<P>::acc;
   const int lane = threadIdx.x, s = threadIdx.y;
   const int tid = lane + 32 * s;
@@ -343,7 +440,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   const long site = tile * 32 + lane;
   int seg, ntl, jl, vh;
   long first;
-  double l_alpha = a.l_alpha, l_beta = a.l_beta, mf = a.mf;
   const void* post = a.post;
   if (a.tile_seg) {
     seg = __ldg(a.tile_seg + tile);
@@ -353,9 +449,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     ntl = S.ntiles;
     jl = (int)(tile - first) * 32 + lane;
     vh = S.Vh;
-    l_alpha = S.l_alpha;
-    l_beta = S.l_beta;
-    mf = S.mf;
     if (POST) post = S.mat[a.post_which];
   } else {
     if (a.stop && *a.stop) return;
@@ -367,18 +460,43 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     vh = a.Vhb;
   }
   const bool valid = jl < vh;
+  // this tile's fifth-dimension coefficients (per problem when batched), read where used
+  auto K5 = [&]() -> Coef5<A> { return a.tile_seg ? coef5<A>(a.segp[seg]) : coef5<A>(a); };
 
   Spinor<A> acc;
   zero(acc);
-  if constexpr (P == P16 || P == PB16) {
+  if constexpr (G == G_RING_CA || G == G_RING_CG) {
     if (valid) {
       const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
-      Hop16<P, DAG, BLOCKED> hp{a, site, lsite, s, tid, NT,
-                                reinterpret_cast<uint4*>(smem_raw)};
+      HopRing<P, DAG, BLOCKED, G == G_RING_CA> hp{a, site, lsite, s, tid, NT,
+                                                  reinterpret_cast<uint4*>(smem_raw)};
       hp.run(acc);
     }
     // the post stage reuses shared memory that other threads' rings occupy
     __syncthreads();
+  } else if (G == G_PF) {
+    if (valid) {
+      const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
+      uint32_t nb[8];
+#pragma unroll
+      for (int d = 0; d < 8; d++) nb[d] = __ldg(a.nbr + (long)d * a.Vp + site);
+      prefetch_nbr<P, BLOCKED>(a, nb[0], s);
+      prefetch_nbr<P, BLOCKED>(a, nb[1], s);
+      hop_dir_nb<P, 0, DAG, BLOCKED>(acc, a, nb[0], lsite, s);
+      prefetch_nbr<P, BLOCKED>(a, nb[2], s);
+      hop_dir_nb<P, 1, DAG, BLOCKED>(acc, a, nb[1], lsite, s);
+      prefetch_nbr<P, BLOCKED>(a, nb[3], s);
+      hop_dir_nb<P, 2, DAG, BLOCKED>(acc, a, nb[2], lsite, s);
+      prefetch_nbr<P, BLOCKED>(a, nb[4], s);
+      hop_dir_nb<P, 3, DAG, BLOCKED>(acc, a, nb[3], lsite, s);
+      prefetch_nbr<P, BLOCKED>(a, nb[5], s);
+      hop_dir_nb<P, 4, DAG, BLOCKED>(acc, a, nb[4], lsite, s);
+      prefetch_nbr<P, BLOCKED>(a, nb[6], s);
+      hop_dir_nb<P, 5, DAG, BLOCKED>(acc, a, nb[5], lsite, s);
+      prefetch_nbr<P, BLOCKED>(a, nb[7], s);
+      hop_dir_nb<P, 6, DAG, BLOCKED>(acc, a, nb[6], lsite, s);
+      hop_dir_nb<P, 7, DAG, BLOCKED>(acc, a, nb[7], lsite, s);
+    }
   } else if (valid) {
     const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
     hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
@@ -392,15 +510,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   }
 
   if constexpr (POST == 2 && (P == P16 || P == PB16)) {
-    post_tensor_core<LS>(acc, a, lane, s, tid, smem_raw, tc_mbar, tc_slot);
+    post_tensor_core<LS>(acc, a, lane, s, tid, smem_raw, tc_mbar, tc_slot, tc_phase);
   }
   if constexpr (POST == 3) {
     // D+^dag h at s = b h_s + c (P+ h_{s+1} + P- h_{s-1}),  h_{Ls} = -mf h_0, h_{-1} = -mf h_{Ls-1}
-    double db = a.dp_b, dc = a.dp_c;
-    if (a.tile_seg) {
-      db = a.segp[seg].db;
-      dc = a.segp[seg].dc;
-    }
     A* buf = reinterpret_cast<A*>(smem_raw);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -408,9 +521,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       buf[(s * 24 + 2 * k + 1) * 32 + lane] = acc.c[k].y;
     }
     __syncthreads();
+    const Coef5<A> C = K5();
     const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
-    const A fu = (s + 1 < LS) ? A(1) : A(-mf), fd = (s > 0) ? A(1) : A(-mf);
-    const A b_ = A(db), c_ = A(dc);
+    const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
+    const A b_ = C.db, c_ = C.dc;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       const int sn = k < 6 ? su : sd;
@@ -426,11 +540,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     // recurrence w and the Sherman-Morrison correction for the corner:
     //   lower: w_0 = v_0, w_s = v_s - r w_{s-1},  z_s = w_s + kappa (-r)^s w_{Ls-1},
     //   upper: mirror image, kappa = r mf / (1 + mf (-r)^Ls);  M5op^-1 v = z / alpha.
-    double db = a.dp_b, dc = a.dp_c;
-    if (a.tile_seg) {
-      db = a.segp[seg].db;
-      dc = a.segp[seg].dc;
-    }
     A* buf = reinterpret_cast<A*>(smem_raw);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -438,11 +547,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       buf[(s * 24 + 2 * k + 1) * 32 + lane] = acc.c[k].y;
     }
     __syncthreads();
-    const A r = A(l_beta / l_alpha), inva = A(1.0 / l_alpha);
-    A pw = A(1);
-    for (int i = 0; i < LS; i++) pw *= -r;
-    const A kappa = r * A(mf) / (A(1) + A(mf) * pw);
-    const A b_ = A(db), c_ = A(dc), mfA = A(mf), pre = A(a.post_pre);
+    const Coef5<A> C = K5();
+    const A r = C.r, inva = C.inva, kappa = C.kappa;
+    const A b_ = C.db, c_ = C.dc, mfA = C.mf, pre = C.pre;
     for (int col = tid; col < 24 * 32; col += NT) {
       const int c = col >> 5, l = col & 31;
       const bool lower = ((c < 12) != DAG);
@@ -537,7 +644,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
   }
 
-  const A hs = A(a.hop_scale);
+  A hs;
+  if constexpr (sizeof(A) == 8) hs = a.hop_scale; else hs = a.hs32;
 #pragma unroll
   for (int k = 0; k < 12; k++) acc.c[k] = cscale(hs, acc.c[k]);
 
@@ -549,9 +657,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     load_spinor<P>(x0, a.in2, a.Vp, site, s);
     load_spinor<P>(xu, a.in2, a.Vp, site, s + 1 < LS ? s + 1 : 0);
     load_spinor<P>(xd, a.in2, a.Vp, site, s > 0 ? s - 1 : LS - 1);
-    const A fu = (s + 1 < LS) ? A(1) : A(-mf);
-    const A fd = (s > 0) ? A(1) : A(-mf);
-    const A la = A(l_alpha), lb = A(l_beta);
+    const Coef5<A> C = K5();
+    const A fu = (s + 1 < LS) ? A(1) : -C.mf;
+    const A fd = (s > 0) ? A(1) : -C.mf;
+    const A la = C.la, lb = C.lb;
     const bool dagm = (a.local_mode == LOC_M5DAG);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -582,8 +691,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     for (int k = 0; k < 12; k++) part = fma(back.c[k].x, back.c[k].x, fma(back.c[k].y, back.c[k].y, part));
     nrm = (double)part;
   } else {
-    store_spinor<P>(a.out, a.Vp, site, s, acc);
-    if (a.epi == EPI_NORM) {
+    if (a.epi != EPI_NORM_ONLY) store_spinor<P>(a.out, a.Vp, site, s, acc);
+    if (a.epi == EPI_NORM || a.epi == EPI_NORM_ONLY) {
       A part = A(0);
 #pragma unroll
       for (int k = 0; k < 12; k++) part = fma(acc.c[k].x, acc.c[k].x, fma(acc.c[k].y, acc.c[k].y, part));
@@ -598,28 +707,31 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
 
 // MINB = resident CTAs per SM the register budget is sized for (2 or 3); the launcher's
 // autotuner picks the faster one per kernel configuration.
-template <int P, int LS, bool DAG, bool BLOCKED, int POST, int MINB>
+// G: how the neighbours are gathered (enum Gather).
+template <int P, int LS, bool DAG, bool BLOCKED, int POST, int MINB, int G>
 __global__ void __launch_bounds__(32 * LS, MINB) stage_kernel(const StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red_scratch[32];
   __shared__ uint64_t tc_mbar;
   __shared__ uint32_t tc_slot;
+  constexpr bool TC = (POST == 2 && (P == P16 || P == PB16));
+  if constexpr (TC) tc_setup<LS>(a, smem_raw, &tc_mbar, &tc_slot);
+  uint32_t tc_phase = 0;
   for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    stage_tile<P, LS, DAG, BLOCKED, POST>(a, tile, smem_raw, red_scratch, &tc_mbar, &tc_slot);
+    stage_tile<P, LS, DAG, BLOCKED, POST, G>(a, tile, smem_raw, red_scratch, &tc_mbar,
+                                             &tc_slot, tc_phase);
     __syncthreads();
   }
+  if constexpr (TC) tc_teardown(&tc_slot);
 }
 
 template <int P>
-size_t stage_smem_bytes(int Ls, int post) {
-  const size_t ring = (P == P16 || P == PB16) ? ring_bytes16(Ls) : 0;
+size_t stage_smem_bytes(int Ls, int post, int gather) {
+  const size_t ring = (gather == G_RING_CA || gather == G_RING_CG) ? ring_bytes<P>(Ls) : 0;
   size_t need = 0;
   if (post == 1) need = (size_t)(Ls * 24 * 32 + 2 * Ls * Ls) * sizeof(typename Prec<P>::acc);
   if (post == 3 || post == 4) need = (size_t)Ls * 24 * 32 * sizeof(typename Prec<P>::acc);
-  if (post == 2) {
-    need = 6 * tc::TILE_BYTES + 2 * tc::B_BYTES;   // operands, then staged results
-    if ((size_t)Ls * 24 * 32 * 4 > need) need = (size_t)Ls * 24 * 32 * 4;
-  }
+  if (post == 2) need = tc_offset(Ls) + 6 * tc::TILE_BYTES + 2 * tc::B_BYTES;
   return need > ring ? need : ring;
 }
 

@@ -1,8 +1,9 @@
-// Launch/dispatch of the stage kernel for one storage precision (included by stage_f*.cu so
-// that the precisions compile in parallel).
+// Launch of the stage kernel variants and their online autotuner (included by stage_ls.cu,
+// which is compiled once per storage precision and Ls).
 #pragma once
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <map>
 
@@ -10,9 +11,9 @@
 
 namespace dwf {
 
-template <int P, int LS, bool DAG, bool BLK, int POST, int MINB>
+template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G>
 static cudaError_t stage_launch_v(const StageArgs& b, size_t sm, long g, cudaStream_t st) {
-  auto k = stage_kernel<P, LS, DAG, BLK, POST, MINB>;
+  auto k = stage_kernel<P, LS, DAG, BLK, POST, MINB, G>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -23,97 +24,172 @@ static cudaError_t stage_launch_v(const StageArgs& b, size_t sm, long g, cudaStr
   return cudaGetLastError();
 }
 
-// Online autotuner of the register budget (2 or 3 resident CTAs per SM): the first launches
-// of each (kernel, problem size) alternate between the two variants bracketed by CUDA
-// events; once both have been timed twice the faster one is used for good.  The timed
-// launches are the caller's real work, so tuning costs nothing extra.  Tuning happens
-// outside stream capture only (a captured launch uses the current choice).
+// Online autotuner over the launch variants of one stage (register budget for 2 or 3
+// resident CTAs per SM and, where both apply, tensor-core or recurrence post): the first
+// launches of each (stage kind, problem size) cycle through the candidates bracketed by CUDA
+// events; once every candidate has been timed twice the fastest is used for good.  The timed
+// launches are the caller's real work, so tuning costs nothing extra.  Tuning happens outside
+// stream capture only (a captured launch uses the current choice), and only on launches
+// without a stop flag; until a kind is decided, other launches use the first candidate.
+using StageFn = cudaError_t (*)(const StageArgs&, size_t, long, cudaStream_t);
+struct StageCand {
+  StageFn fn;
+  size_t smem;
+  int per_sm;            // 0: one CTA per tile; k: persistent grid of k CTAs per SM
+  int post, minb, gather;  // for the tuning log
+};
+constexpr int MAX_CANDS = 12;
+constexpr int TUNE_ROUNDS = 2;   // timed rounds after one untimed round (first-launch costs)
 struct StageTune {
   int next = 0;          // launches recorded so far
-  int chosen = -1;       // decided variant (0: 2 CTAs/SM, 1: 3 CTAs/SM)
-  cudaEvent_t ev[8] = {};
+  int chosen = -1;       // decided candidate
+  cudaEvent_t ev[2 * TUNE_ROUNDS * MAX_CANDS] = {};
   bool pending = false;
 };
 
+// The variants timed per stage kind: FP32 gathers into registers, through the cp.async ring
+// (L1-cached) or into registers with L1 prefetch, each as one CTA per tile or a persistent
+// grid of 2 CTAs per SM (a budget for 3 CTAs per SM spills); FP16/BF16 always use the ring
+// (L1-cached or L2-only) with a register budget for 2 or 3 CTAs per SM; FP64 (ALU bound)
+// one CTA per tile or persistent.
+template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G>
+static void stage_cand(StageCand* c, int& n, int per_sm) {
+  c[n++] = {stage_launch_v<P, LS, DAG, BLK, POST, MINB, G>,
+            stage_smem_bytes<P>(LS, POST, G), per_sm, POST, MINB, G};
+}
 template <int P, int LS, bool DAG, bool BLK, int POST>
-static cudaError_t stage_launch_post(const StageArgs& a, cudaStream_t st) {
-  const size_t sm = stage_smem_bytes<P>(LS, POST);
+static void stage_cands(StageCand* c, int& n) {
+  if constexpr (P == P16 || P == PB16) {
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CG>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CG>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 3);
+  } else if constexpr (P == P32) {
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_PF>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_PF>(c, n, 2);
+  } else {
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);
+  }
+}
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+  }
+  return n;
+}
+
+template <int P, int LS, bool DAG, bool BLK>
+static cudaError_t stage_launch_one(const StageArgs& a, cudaStream_t st) {
+  constexpr bool H16 = (P == P16 || P == PB16);
+  StageCand c[MAX_CANDS];
+  int n = 0, kind;
+  if (!a.post) {
+    kind = 0;
+    stage_cands<P, LS, DAG, BLK, 0>(c, n);
+  } else if (a.post_sparse) {
+    kind = 3;
+    stage_cands<P, LS, DAG, BLK, 3>(c, n);
+  } else if (H16 && a.post_h && a.post_struct == 2) {
+    kind = 5;
+    stage_cands<P, LS, DAG, BLK, 2>(c, n);
+    stage_cands<P, LS, DAG, BLK, 4>(c, n);
+  } else if (a.post_struct) {
+    kind = 4;
+    stage_cands<P, LS, DAG, BLK, 4>(c, n);
+  } else if (H16 && a.post_h) {
+    kind = 2;
+    stage_cands<P, LS, DAG, BLK, 2>(c, n);
+  } else {
+    kind = 1;
+    stage_cands<P, LS, DAG, BLK, 1>(c, n);
+  }
   StageArgs b = a;
   if (b.ntiles == 0) b.ntiles = b.Vp / 32;
-  const long g = b.grid > 0 ? std::min<long>(b.grid, b.ntiles) : b.ntiles;
-  static std::map<long, StageTune> tunes;   // per tile count
-  StageTune& T = tunes[b.ntiles];
+  // an explicit grid (batched solver) is kept; otherwise the candidate decides
+  auto grid_of = [&](const StageCand& k) -> long {
+    if (b.grid > 0) return std::min<long>(b.grid, b.ntiles);
+    return k.per_sm ? std::min<long>((long)k.per_sm * sm_count(), b.ntiles) : b.ntiles;
+  };
+  static std::map<std::pair<long, int>, StageTune> tunes;   // per (tile count, kind)
+  StageTune& T = tunes[{b.ntiles, kind}];
+  const int nt = TUNE_ROUNDS * n;                           // timed launches
+  const int nl = nt + n;                                    // tuning launches
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cap);
   const bool capturing = (cap != cudaStreamCaptureStatusNone);
   // event queries are not allowed while the stream is being captured: decide only outside
-  if (!capturing && T.chosen < 0 && T.next >= 4 && T.pending) {
-    // decide once every timed launch has completed
+  if (!capturing && T.chosen < 0 && T.next >= nl && T.pending) {
     bool done = true;
-    for (int i = 0; i < 8; i++) done = done && cudaEventQuery(T.ev[i]) == cudaSuccess;
+    for (int i = 0; i < 2 * nt; i++) done = done && cudaEventQuery(T.ev[i]) == cudaSuccess;
     cudaGetLastError();
     if (done) {
-      float t[4];
-      for (int i = 0; i < 4; i++) cudaEventElapsedTime(&t[i], T.ev[2 * i], T.ev[2 * i + 1]);
-      T.chosen = (t[1] + t[3] < t[0] + t[2]) ? 1 : 0;
-      for (auto& e : T.ev) cudaEventDestroy(e);
+      float best = 0.f, tks[MAX_CANDS];
+      for (int k = 0; k < n; k++) {
+        float tk = 0.f;
+        for (int i = k; i < nt; i += n) {
+          float t = 0.f;
+          cudaEventElapsedTime(&t, T.ev[2 * i], T.ev[2 * i + 1]);
+          tk += t;
+        }
+        tks[k] = tk;
+        if (T.chosen < 0 || tk < best) {
+          best = tk;
+          T.chosen = k;
+        }
+      }
+      if (getenv("DWF_TUNE_LOG")) {   // one line per decision: every candidate's time
+        fprintf(stderr, "dwf tune P%d Ls%d dag%d blk%d tiles %ld:", P, LS, (int)DAG, (int)BLK,
+                b.ntiles);
+        for (int k = 0; k < n; k++)
+          fprintf(stderr, " %s[post%d minb%d gather%d sm%d %.1fus]", k == T.chosen ? "*" : "",
+                  c[k].post, c[k].minb, c[k].gather, c[k].per_sm, 1000.f * tks[k] / TUNE_ROUNDS);
+        fprintf(stderr, "\n");
+      }
+      for (auto& e : T.ev)
+        if (e) cudaEventDestroy(e);
       T.pending = false;
     }
   }
   const char* force = getenv("DWF_STAGE_VARIANT");
   int v = T.chosen >= 0 ? T.chosen : 0;
-  if (force && (force[0] == '0' || force[0] == '1')) {
+  if (force && force[0] >= '0' && force[0] < '0' + n && force[1] == 0) {
     v = force[0] - '0';
-  } else if (T.chosen < 0 && T.next < 4 && !capturing) {
+  } else if (T.chosen < 0 && T.next < nl && !capturing && a.stop == nullptr) {
+    // launches that may return early (a solver's stop flag) are never timed: a converged
+    // cycle would make the candidate that ran then look fast
     if (T.next == 0)
-      for (auto& e : T.ev) cudaEventCreate(&e);
-    v = T.next & 1;
-    cudaEventRecord(T.ev[2 * T.next], st);
-    cudaError_t e = v ? stage_launch_v<P, LS, DAG, BLK, POST, 3>(b, sm, g, st)
-                      : stage_launch_v<P, LS, DAG, BLK, POST, 2>(b, sm, g, st);
-    cudaEventRecord(T.ev[2 * T.next + 1], st);
+      for (int i = 0; i < 2 * nt; i++) cudaEventCreate(&T.ev[i]);
+    v = T.next % n;
+    const int j = T.next - n;   // timed launch index (the first round is not timed)
+    if (j >= 0) cudaEventRecord(T.ev[2 * j], st);
+    cudaError_t e = c[v].fn(b, c[v].smem, grid_of(c[v]), st);
+    if (j >= 0) cudaEventRecord(T.ev[2 * j + 1], st);
     T.next++;
     T.pending = true;
     return e;
   }
-  return v ? stage_launch_v<P, LS, DAG, BLK, POST, 3>(b, sm, g, st)
-           : stage_launch_v<P, LS, DAG, BLK, POST, 2>(b, sm, g, st);
-}
-
-template <int P, int LS, bool DAG, bool BLK>
-static cudaError_t stage_launch_one(const StageArgs& a, cudaStream_t st) {
-  if (!a.post) return stage_launch_post<P, LS, DAG, BLK, 0>(a, st);
-  if (a.post_sparse) return stage_launch_post<P, LS, DAG, BLK, 3>(a, st);
-  if constexpr (P == P64 || P == P32) {
-    if (a.post_struct) return stage_launch_post<P, LS, DAG, BLK, 4>(a, st);
-  }
-  if constexpr (P == P16 || P == PB16) {
-    if (a.post_h) return stage_launch_post<P, LS, DAG, BLK, 2>(a, st);
-  }
-  return stage_launch_post<P, LS, DAG, BLK, 1>(a, st);
+  return c[v].fn(b, c[v].smem, grid_of(c[v]), st);
 }
 
 template <int P, int LS>
-static cudaError_t stage_dispatch_ls(const StageArgs& a, bool dag, bool blocked,
-                                     cudaStream_t st) {
+cudaError_t stage_dispatch_ls(const StageArgs& a, bool dag, bool blocked, cudaStream_t st) {
   if (dag)
     return blocked ? stage_launch_one<P, LS, true, true>(a, st)
                    : stage_launch_one<P, LS, true, false>(a, st);
   return blocked ? stage_launch_one<P, LS, false, true>(a, st)
                  : stage_launch_one<P, LS, false, false>(a, st);
-}
-
-template <int P>
-cudaError_t launch_stage(const StageArgs& a, int Ls, bool dag, bool blocked, cudaStream_t st) {
-  switch (Ls) {
-    case 4: return stage_dispatch_ls<P, 4>(a, dag, blocked, st);
-    case 6: return stage_dispatch_ls<P, 6>(a, dag, blocked, st);
-    case 8: return stage_dispatch_ls<P, 8>(a, dag, blocked, st);
-    case 10: return stage_dispatch_ls<P, 10>(a, dag, blocked, st);
-    case 12: return stage_dispatch_ls<P, 12>(a, dag, blocked, st);
-    case 16: return stage_dispatch_ls<P, 16>(a, dag, blocked, st);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 }  // namespace dwf

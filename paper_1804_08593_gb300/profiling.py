@@ -1,18 +1,27 @@
-"""Summarises ncu output into the short text tables kept in this folder.
+"""Helpers for the ncu summaries kept under profiles/ and for bench.py's roofline entry.
 
-  python profiles/summarize_ncu.py launches <launches.csv>   # per-kernel launches, time, share
-  python profiles/summarize_ncu.py report <file.ncu-rep>     # key counters per captured launch
+  python -m paper_1804_08593_gb300.profiling launches <launches.csv>  # per kernel: launches, time, share
+  python -m paper_1804_08593_gb300.profiling report <file.ncu-rep>    # key counters per captured launch
+  python -m paper_1804_08593_gb300.profiling sha                      # hash of the stage-kernel sources
 
 The launch list comes from
   ncu --metrics gpu__time_duration.sum --clock-control none -c <N> --csv --log-file <csv> <cmd>
 and the report from
   ncu --set full --clock-control none -k regex:<kernel> -s <n> -c <m> -o <file> <cmd>.
+A summary that records DRAM traffic per launch carries a line
+  traffic: <kernel class> <bytes per launch> <sha>
+where <sha> is stage_sources_sha() at capture time; bench.py reports the traffic only while
+the stage sources still hash to it.
 """
 from __future__ import annotations
 
 import collections
 import csv
+import glob
+import hashlib
 import io
+import os
+import re
 import subprocess
 import sys
 
@@ -24,6 +33,11 @@ COUNTERS = [
     "smsp__inst_executed.sum", "l1tex__t_sector_hit_rate.pct", "lts__t_sector_hit_rate.pct",
     "sm__pipe_tensor_cycles_active.avg.pct_of_peak_sustained_active",
     "smsp__average_warps_issue_stalled_long_scoreboard_per_issue_active.ratio",
+    "smsp__issue_active.avg.pct_of_peak_sustained_active",
+    "sm__inst_executed_pipe_fma.avg.pct_of_peak_sustained_active",
+    "sm__inst_executed_pipe_fp64.avg.pct_of_peak_sustained_active",
+    "sm__inst_executed_pipe_lsu.avg.pct_of_peak_sustained_active",
+    "launch__grid_size",
 ]
 
 
@@ -64,8 +78,45 @@ def report(path: str) -> None:
             if c in hdr:
                 i = hdr.index(c)
                 print(f"| {c} | {r[i]} {units[i]} |")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+        dram = 0.0
+        for c in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            if c in hdr:
+                i = hdr.index(c)
+                dram += float(r[i].replace(",", "")) * scale.get(units[i], 1)
+        print(f"| DRAM bytes (read + write) | {dram:.0f} |")
         print()
 
 
+HERE = os.path.dirname(os.path.abspath(__file__))
+STAGE_SOURCES = ("stage.cuh", "stage_inst.cuh", "stage_ls.cu", "dwf_device.cuh", "tc_m5.cuh")
+
+
+def stage_sources_sha() -> str:
+    """First 16 hex digits of the SHA-256 of the stage-kernel sources."""
+    h = hashlib.sha256()
+    for name in STAGE_SOURCES:
+        with open(os.path.join(HERE, "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_class: str, profiles_dir: str):
+    """DRAM bytes per launch recorded for a kernel class in profiles/*.md, or None when none is
+    recorded or the stage sources changed since the capture."""
+    sha = stage_sources_sha()
+    pat = re.compile(r"^traffic:\s+(\S+)\s+(\d+)\s+([0-9a-f]+)\s*$")
+    for path in sorted(glob.glob(os.path.join(profiles_dir, "*.md"))):
+        with open(path) as f:
+            for line in f:
+                m = pat.match(line.strip().strip("`"))
+                if m and m.group(1) == kernel_class and m.group(3) == sha:
+                    return int(m.group(2))
+    return None
+
+
 if __name__ == "__main__":
-    {"launches": launches, "report": report}[sys.argv[1]](sys.argv[2])
+    if sys.argv[1] == "sha":
+        print(stage_sources_sha())
+    else:
+        {"launches": launches, "report": report}[sys.argv[1]](sys.argv[2])

@@ -21,6 +21,8 @@ CASES = [
     ((4, 4, 4, 8), 12, 1.8, 0.005, 1.5, 0.5, 0.35),  # Ls = 12 Moebius
     ((4, 4, 4, 4), 16, 1.8, 0.01, 1.0, 0.0, 0.3),    # Ls = 16 Shamir
     ((4, 4, 2, 2), 10, 1.6, 0.2, 2.0, 1.0, 0.5),     # Ls = 10, b - c != 1... general b, c
+    ((4, 4, 2, 4), 8, 1.8, 0.1, 1.25, 0.0, 0.3),     # c = 0, b != 1: D+ = b absorbed
+    ((4, 2, 4, 4), 6, 1.8, 0.1, 0.5, 1.5, 0.3),      # |beta/alpha| > 1: matrices only
 ]
 
 
@@ -130,6 +132,7 @@ def test_tensor_core_m5_matches_cuda_core_path(case, prec, monkeypatch):
     x = rand_even(rng, p.dims, p.Ls)
     ref = o.mdagm(U, x, p)
     outs = {}
+    monkeypatch.setenv("DWF_POST", "matrix")   # no recurrence candidate: TC vs CUDA cores
     for flag in ("0", "1"):
         monkeypatch.setenv("DWF_DISABLE_TC", flag)
         h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
@@ -139,3 +142,22 @@ def test_tensor_core_m5_matches_cuda_core_path(case, prec, monkeypatch):
         assert rel(outs[flag], ref) <= TOL[prec], (flag, rel(outs[flag], ref))
     # both round the result to the same 16-bit storage, so they agree to that precision
     assert rel(outs["0"], outs["1"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("case", [CASES[1], CASES[2], CASES[4], CASES[6], CASES[7]])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("mode", ["matrix", "recurrence"])
+def test_post_by_matrix_and_by_recurrence(case, prec, mode, monkeypatch):
+    """D+ M5op^-1 and M5op^-dag D+^dag are applied either as dense Ls x Ls matrices or by the
+    O(Ls) bidiagonal recurrences with the Sherman-Morrison wall correction (DWF_POST at
+    handle creation).  Both must meet the operator tolerance for Mpc, Mpc^dag and MdagM."""
+    dwf = lib()
+    rng, U, p = _setup(case, 11)
+    x = rand_even(rng, p.dims, p.Ls)
+    monkeypatch.setenv("DWF_POST", mode)
+    h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
+    for op, ref in (("Mpc", o.mpc(U, x, p)), ("Mpc_dag", o.mpc_dag(U, x, p)),
+                    ("MdagM", o.mdagm(U, x, p))):
+        out = cuda(np.zeros_like(x))
+        dwf.dwf_apply(h, op, cuda(x), out, prec)
+        assert rel(host(out), ref) <= TOL[prec], (op, rel(host(out), ref))

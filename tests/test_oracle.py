@@ -583,3 +583,19 @@ def test_action_estimator_against_dense_solve():
     e = 1e-4 * (rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape))
     err = abs(o.action(U, phi, p, X=(x + e).reshape(phi.shape)) - S)
     assert err <= 1.01 * float(np.vdot(e, A @ e).real) + 1e-12
+
+
+@pytest.mark.parametrize("dims,b,c", [((4, 4, 2, 4), 1.5, 0.5), ((2, 4, 4, 2), 1.0, 0.0)])
+def test_site_sampled_mpc_equals_whole_lattice(dims, b, c):
+    """mpc_at_sites (used to check full-size lattices at sampled sites) restates Mpc and
+    Mpc^dag site by site; it must agree with the whole-lattice functions at every sampled
+    site, including lattices two sites wide where the +mu and -mu neighbours coincide."""
+    rng = np.random.default_rng(31)
+    p = o.DWFParams(dims, 6, 1.8, 0.05, b, c)
+    U = inputs.gauge_links(dims, 0.3, rng)
+    n = int(np.prod(dims)) // 2
+    x = rng.standard_normal((6, n, 4, 3)) + 1j * rng.standard_normal((6, n, 4, 3))
+    sites = [0, 5, 17, n - 1]
+    for dag, full in ((False, o.mpc(U, x, p)), (True, o.mpc_dag(U, x, p))):
+        part = o.mpc_at_sites(U, x, p, sites, dag)
+        assert np.abs(part - full[:, sites]).max() <= 1e-13 * np.abs(full).max()
