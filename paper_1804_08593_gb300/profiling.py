@@ -89,7 +89,7 @@ def report(path: str) -> None:
 
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-STAGE_SOURCES = ("stage.cuh", "stage_inst.cuh", "stage_ls.cu", "dwf_device.cuh", "tc_m5.cuh")
+STAGE_SOURCES = ("stage.cuh", "dwf_device.cuh", "tc_m5.cuh")   # the kernel code itself
 
 
 def stage_sources_sha() -> str:
