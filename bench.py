@@ -56,6 +56,9 @@ def args_parse():
     ap.add_argument("--case", default="solve", choices=["solve", "apply"],
                     help="apply: only K applications of Mpc^dag Mpc (for profiler captures)")
     ap.add_argument("--prec", default="f16", help="precision of --case apply")
+    ap.add_argument("--dims", default=None,
+                    help="X,Y,Z,T: a smaller lattice with the workload's other parameters, for "
+                         "profiler captures (the JSON line then names that lattice)")
     return ap.parse_args()
 
 
@@ -177,6 +180,19 @@ def barrier(ws):
         dist.barrier()
 
 
+def max_over_ranks(value: float, ws: int) -> float:
+    """Largest per-rank value over all ranks: every rank solves its own replica, so the job's
+    time is the slowest rank's (NCCL reduces on the GPU, gloo on the host)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(a):
     ws, rank, local = dist_init()
     if rank != 0:
@@ -204,6 +220,23 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def load_workload(a):
+    """The benchmark workload's parameters and fields (links, source); --dims swaps in another
+    lattice drawn the same way (same seed and link spread)."""
+    import numpy as np
+
+    from paper_1804_08593_gb300 import inputs
+    if not a.dims:
+        return dict(inputs.CONFIGS[WORKLOAD]), inputs.workload(WORKLOAD)
+    cfg = dict(inputs.CONFIGS[WORKLOAD])
+    cfg["dims"] = tuple(int(v) for v in a.dims.split(","))
+    rng = np.random.default_rng(cfg["seed"])
+    w = dict(cfg)
+    w["links"] = inputs.gauge_links(cfg["dims"], cfg["eps"], rng)
+    w["phi"] = inputs.even_source(cfg["dims"], cfg["Ls"], rng)
+    return cfg, w
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -216,8 +249,7 @@ def run_ours(a):
     torch.cuda.set_device(local)
     build.build()
     dwf.load()
-    cfg = inputs.CONFIGS[WORKLOAD]
-    w = inputs.workload(WORKLOAD)
+    cfg, w = load_workload(a)
     stream = torch.cuda.current_stream()
     links_d = torch.from_numpy(w["links"]).cuda()
     phi_d = torch.from_numpy(w["phi"]).cuda()
@@ -253,11 +285,7 @@ def run_ours(a):
     prof = dwf.dwf_profile_read(h)
     ms = ev0.elapsed_time(ev1)
     t_step = ms / 1e3 / a.steps
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt)
+    t_step = max_over_ranks(t_step, ws)
 
     # roofline of the dominant kernel class
     pk, pk_kind = peaks()
@@ -337,7 +365,8 @@ def run_ours(a):
         "warmup": a.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": f"{a.inner}/f32/f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": "24x24x24x48", "Ls": cfg["Ls"],
+        "config": {"workload": WORKLOAD if not a.dims else WORKLOAD + " at " + a.dims,
+                   "lattice": "x".join(str(v) for v in cfg["dims"]), "Ls": cfg["Ls"],
                    "solver": f"mspcg_{a.local_op}", "block": "6x6x6x6", "l": a.l,
                    "inner": a.inner, "middle": "f32", "outer": "f64", "tol": TOL,
                    "parallelism": "replicas" if ws > 1 else "single",
@@ -381,8 +410,7 @@ def run_apply(a):
     from paper_1804_08593_gb300 import build, dwf, inputs
     torch.cuda.set_device(0)
     build.build()
-    cfg = inputs.CONFIGS[WORKLOAD]
-    w = inputs.workload(WORKLOAD)
+    cfg, w = load_workload(a)
     h = dwf.dwf_create(cfg["dims"], cfg["Ls"], cfg["M5"], cfg["mf"], cfg["b"], cfg["c"],
                        torch.from_numpy(w["links"]).cuda())
     phi = torch.from_numpy(w["phi"]).cuda()

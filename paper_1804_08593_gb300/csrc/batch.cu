@@ -566,11 +566,15 @@ dwf_status autotune(Group& G, cudaStream_t st) {
   int best_grid = 0;
   for (int c : cand) {
     G.grid = c ? c * sms : 0;
-    StageArgs a = gbase(G, P32, 1, nullptr);
+    // the stage A launch of a CG step, with the problems' stop flags like the real launches
+    // (the per-stage variant tuner never times launches that carry stop flags)
+    StageArgs a = gbase(G, P32, 1, G.fl + FL_STOP * G.nseg);
     a.in = G.f32[3];
     a.out = G.f32[4];
     a.post = G.mats[1];
     a.post_which = 0;
+    a.post_struct = G.post_struct;
+    a.post_pre = 1.0;
     DWF_CUDA(launch_stage_prec(P32, a, G.Ls, false, false, st));   // warm
     DWF_CUDA(cudaEventRecord(e0, st));
     for (int r = 0; r < 3; r++) DWF_CUDA(launch_stage_prec(P32, a, G.Ls, false, false, st));

@@ -206,13 +206,12 @@ __global__ void cast_kernel(const CastArgs a) {
 #pragma unroll
       for (int k = 0; k < 12; k++) part = fma(w.c[k].x, w.c[k].x, fma(w.c[k].y, w.c[k].y, part));
     }
-    const double acc = (double)part;
-    double vv[1] = {acc};
+    AO vv[1] = {part};
     if (a.tile_seg)
-      grid_reduce_seg<1>(a.red, vv, scratch, blockIdx.x, seg, a.segp[seg].first_tile,
-                         a.segp[seg].ntiles);
+      grid_reduce_seg<1, AO>(a.red, vv, scratch, blockIdx.x, seg, a.segp[seg].first_tile,
+                             a.segp[seg].ntiles);
     else
-      grid_reduce<1>(a.red, vv, scratch);
+      grid_reduce<1, AO>(a.red, vv, scratch);
   }
 }
 
@@ -328,10 +327,10 @@ __global__ void vop_kernel(const VopArgs a) {
   if (a.red.partial) {
     double vv[1] = {acc};
     if (a.tile_seg)
-      grid_reduce_seg<1>(a.red, vv, scratch, blockIdx.x, seg, a.segp[seg].first_tile,
-                         a.segp[seg].ntiles);
+      grid_reduce_seg<1, double>(a.red, vv, scratch, blockIdx.x, seg, a.segp[seg].first_tile,
+                                 a.segp[seg].ntiles);
     else
-      grid_reduce<1>(a.red, vv, scratch);
+      grid_reduce<1, double>(a.red, vv, scratch);
   }
 }
 

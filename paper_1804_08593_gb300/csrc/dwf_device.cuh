@@ -321,15 +321,18 @@ struct RedArgs {
   int hist_cap;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Block-wide sum of NV values per thread; result valid in thread 0.  scratch: >= 32*NV doubles.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
+// Block-wide sum of NV values per thread; result valid in thread 0.  scratch: >= 32*NV values.
+// FP32 kernels sum their CTA in FP32 (GB300's FP64 pipe is narrow) and hand one FP64 partial
+// per CTA to the grid-level sum.
+template <int NV, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* scratch) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
@@ -343,7 +346,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* scratch) {
   if (warp == 0) {
 #pragma unroll
     for (int i = 0; i < NV; i++) {
-      double t = lane < nw ? scratch[lane * NV + i] : 0.0;
+      T t = lane < nw ? scratch[lane * NV + i] : T(0);
       v[i] = warp_sum(t);
     }
   }
@@ -372,16 +375,16 @@ __device__ void finalize_value(const RedArgs& r, int seg, const double (&v)[NV])
 // tile `tile` of segment `seg` whose tiles are [first, first + ntiles).  The last tile of the
 // segment to arrive sums the segment's partials in a fixed order (deterministic) and
 // finalizes.  Returns normally in every thread (usable inside a persistent tile loop).
-template <int NV>
-__device__ void grid_reduce_seg(const RedArgs& r, double (&v)[NV], double* scratch, long tile,
+template <int NV, typename T>
+__device__ void grid_reduce_seg(const RedArgs& r, T (&v)[NV], double* scratch, long tile,
                                 int seg, long first, int ntiles) {
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nthr = blockDim.x * blockDim.y;
-  block_sum<NV>(v, scratch);
+  block_sum<NV, T>(v, reinterpret_cast<T*>(scratch));
   __shared__ unsigned is_last;
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < NV; i++) r.partial[tile * NV + i] = v[i];
+    for (int i = 0; i < NV; i++) r.partial[tile * NV + i] = (double)v[i];
     __threadfence();
     const unsigned prev = atomicAdd(&r.counter[seg], 1u);
     is_last = (prev == (unsigned)ntiles - 1u);
@@ -395,7 +398,7 @@ __device__ void grid_reduce_seg(const RedArgs& r, double (&v)[NV], double* scrat
     for (int k = tid; k < ntiles; k += nthr)
 #pragma unroll
       for (int i = 0; i < NV; i++) s[i] += __ldcg(&r.partial[(first + k) * NV + i]);
-    block_sum<NV>(s, scratch);
+    block_sum<NV, double>(s, scratch);
     if (tid == 0) {
       finalize_value<NV>(r, seg, s);
       r.counter[seg] = 0u;
@@ -405,10 +408,10 @@ __device__ void grid_reduce_seg(const RedArgs& r, double (&v)[NV], double* scrat
 }
 
 // Uniform segments of r.cps tiles (tile = blockIdx.x).
-template <int NV>
-__device__ void grid_reduce(const RedArgs& r, double (&v)[NV], double* scratch) {
+template <int NV, typename T>
+__device__ void grid_reduce(const RedArgs& r, T (&v)[NV], double* scratch) {
   const int seg = blockIdx.x / r.cps;
-  grid_reduce_seg<NV>(r, v, scratch, blockIdx.x, seg, (long)seg * r.cps, r.cps);
+  grid_reduce_seg<NV, T>(r, v, scratch, blockIdx.x, seg, (long)seg * r.cps, r.cps);
 }
 
 // Per-problem description of a batched (concatenated) site space: problem = segment.

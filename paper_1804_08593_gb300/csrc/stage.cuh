@@ -160,7 +160,55 @@ __device__ __forceinline__ void hop_term16(Spinor<float>& acc, const uint4 (&q)[
 // autotuner): straight into registers; through a two-slot cp.async ring in shared memory
 // (caching in L1, or in L2 only); or into registers with the indices loaded up front and
 // direction d+1 prefetched into L1 while direction d is computed.
-enum Gather { G_REG = 0, G_RING_CA = 1, G_PF = 2, G_RING_CG = 3 };
+// G_BPF / G_BPF_LS / G_BPF_L: registers, after one bulk L2 prefetch per tile of what the tile
+// will read: everything (its links, the local-term and residual inputs, the 8 x Ls x chunk runs
+// of neighbour spinors), the links and streamed inputs, or the links only; so no direction
+// waits on DRAM for its links.  G_RING_BPF: links and streams in front of the L1-cached ring.
+enum Gather { G_REG = 0, G_RING_CA = 1, G_PF = 2, G_RING_CG = 3, G_BPF = 4, G_RING_BPF = 5,
+              G_BPF_LS = 6, G_BPF_L = 7 };
+// bulk-prefetch depth of a gather mode (0: none)
+__host__ __device__ constexpr int bpf_what(int g) {
+  return g == G_BPF ? 3 : g == G_BPF_LS ? 2 : g == G_BPF_L ? 1 : g == G_RING_BPF ? 2 : 0;
+}
+
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p), "r"(bytes) : "memory");
+}
+
+// Every run is 32 sites x 16 bytes = 512 bytes starting at a site index in [0, Vp - 32]
+// (tiles cover [0, Vp); a neighbour run starts at the tile's first neighbour and is clamped to
+// the array).  WHAT: 1 the tile's links, 2 also its streamed inputs (local-term input,
+// residual), 3 also the neighbour runs (whole-lattice stages only: halo arrays have absent
+// neighbours).  A bulk prefetch takes warp-uniform operands, so lane 0 of each warp issues
+// its share (a per-lane loop would be serialised lane by lane).
+template <int P, int LS, bool BLOCKED, int WHAT>
+__device__ __forceinline__ void prefetch_tile(const StageArgs& a, long tile) {
+  constexpr int NCH = Prec<P>::NCH, NCHL = Prec<P>::NCHL;
+  constexpr int nrun = LS * NCH;   // (s, chunk) runs of one field
+  const int warp = threadIdx.y, nw = blockDim.y;
+  if (threadIdx.x != 0) return;
+  const long base = tile * 32;
+  const uint4* L = reinterpret_cast<const uint4*>(a.links);
+  for (int i = warp; i < 8 * NCHL; i += nw) prefetch_l2_bulk(L + (long)i * a.Vp_link + base, 512);
+  if constexpr (WHAT >= 2) {
+    if (a.local_mode != LOC_NONE) {
+      const uint4* Y = reinterpret_cast<const uint4*>(a.in2);
+      for (int i = warp; i < nrun; i += nw) prefetch_l2_bulk(Y + (long)i * a.Vp + base, 512);
+    }
+    if (a.epi == EPI_CG_R) {
+      const uint4* R = reinterpret_cast<const uint4*>(a.r);
+      for (int i = warp; i < nrun; i += nw) prefetch_l2_bulk(R + (long)i * a.Vp + base, 512);
+    }
+  }
+  if constexpr (WHAT >= 3 && !BLOCKED) {
+    const uint4* X = reinterpret_cast<const uint4*>(a.in);
+    for (int d = 0; d < 8; d++) {
+      long j = (long)(__ldg(a.nbr + (long)d * a.Vp + base) & NBR_IDX);
+      if (j > a.Vp_in - 32) j = a.Vp_in - 32;
+      for (int i = warp; i < nrun; i += nw) prefetch_l2_bulk(X + (long)i * a.Vp_in + j, 512);
+    }
+  }
+}
 
 // source array, site stride and presence of the neighbour behind table entry nb
 template <bool BLOCKED>
@@ -465,15 +513,29 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
 
   Spinor<A> acc;
   zero(acc);
-  if constexpr (G == G_RING_CA || G == G_RING_CG) {
+  if constexpr (G == G_RING_CA || G == G_RING_CG || G == G_RING_BPF) {
+    if constexpr (G == G_RING_BPF) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
     if (valid) {
       const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
-      HopRing<P, DAG, BLOCKED, G == G_RING_CA> hp{a, site, lsite, s, tid, NT,
+      HopRing<P, DAG, BLOCKED, G != G_RING_CG> hp{a, site, lsite, s, tid, NT,
                                                   reinterpret_cast<uint4*>(smem_raw)};
       hp.run(acc);
     }
     // the post stage reuses shared memory that other threads' rings occupy
     __syncthreads();
+  } else if (G == G_BPF || G == G_BPF_LS || G == G_BPF_L) {
+    prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
+    if (valid) {
+      const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
+      hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
+      hop_dir<P, 1, DAG, BLOCKED>(acc, a, site, lsite, s);
+      hop_dir<P, 2, DAG, BLOCKED>(acc, a, site, lsite, s);
+      hop_dir<P, 3, DAG, BLOCKED>(acc, a, site, lsite, s);
+      hop_dir<P, 4, DAG, BLOCKED>(acc, a, site, lsite, s);
+      hop_dir<P, 5, DAG, BLOCKED>(acc, a, site, lsite, s);
+      hop_dir<P, 6, DAG, BLOCKED>(acc, a, site, lsite, s);
+      hop_dir<P, 7, DAG, BLOCKED>(acc, a, site, lsite, s);
+    }
   } else if (G == G_PF) {
     if (valid) {
       const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
@@ -672,7 +734,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
   }
 
-  double nrm = 0.0;
+  A nrm = A(0);   // this thread's share of the reduction, in the accumulation type
   if (a.epi == EPI_CG_R) {
     const A al = A(a.alpha[seg]);
     Spinor<A> rr;
@@ -689,19 +751,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     A part = A(0);   // per-thread partial in the accumulation type; FP64 across threads
 #pragma unroll
     for (int k = 0; k < 12; k++) part = fma(back.c[k].x, back.c[k].x, fma(back.c[k].y, back.c[k].y, part));
-    nrm = (double)part;
+    nrm = part;
   } else {
     if (a.epi != EPI_NORM_ONLY) store_spinor<P>(a.out, a.Vp, site, s, acc);
     if (a.epi == EPI_NORM || a.epi == EPI_NORM_ONLY) {
       A part = A(0);
 #pragma unroll
       for (int k = 0; k < 12; k++) part = fma(acc.c[k].x, acc.c[k].x, fma(acc.c[k].y, acc.c[k].y, part));
-      nrm = (double)part;
+      nrm = part;
     }
   }
   if (a.epi != EPI_STORE) {
-    double v[1] = {nrm};
-    grid_reduce_seg<1>(a.red, v, red_scratch, tile, seg, first, ntl);
+    A v[1] = {nrm};
+    grid_reduce_seg<1, A>(a.red, v, red_scratch, tile, seg, first, ntl);
   }
 }
 
@@ -727,7 +789,8 @@ __global__ void __launch_bounds__(32 * LS, MINB) stage_kernel(const StageArgs a)
 
 template <int P>
 size_t stage_smem_bytes(int Ls, int post, int gather) {
-  const size_t ring = (gather == G_RING_CA || gather == G_RING_CG) ? ring_bytes<P>(Ls) : 0;
+  const size_t ring =
+      (gather == G_RING_CA || gather == G_RING_CG || gather == G_RING_BPF) ? ring_bytes<P>(Ls) : 0;
   size_t need = 0;
   if (post == 1) need = (size_t)(Ls * 24 * 32 + 2 * Ls * Ls) * sizeof(typename Prec<P>::acc);
   if (post == 3 || post == 4) need = (size_t)Ls * 24 * 32 * sizeof(typename Prec<P>::acc);

@@ -47,11 +47,13 @@ struct StageTune {
   bool pending = false;
 };
 
-// The variants timed per stage kind: FP32 gathers into registers, through the cp.async ring
-// (L1-cached) or into registers with L1 prefetch, each as one CTA per tile or a persistent
-// grid of 2 CTAs per SM (a budget for 3 CTAs per SM spills); FP16/BF16 always use the ring
-// (L1-cached or L2-only) with a register budget for 2 or 3 CTAs per SM; FP64 (ALU bound)
-// one CTA per tile or persistent.
+// The variants timed per stage kind.  FP32 gathers into registers, plain or after a bulk L2
+// prefetch of the tile's links (and streamed inputs, and neighbour runs), as one CTA per tile
+// or a persistent grid of 2 CTAs per SM
+// (a register budget for 3 CTAs per SM spills; the cp.async ring and per-direction L1
+// prefetch measured slower and were dropped).  FP16/BF16 gather through the L1-cached
+// cp.async ring, with a register budget for 2 or 3 CTAs per SM, with or without the bulk
+// prefetch, or persistent.  FP64 (ALU bound): one CTA per tile or persistent.
 template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G>
 static void stage_cand(StageCand* c, int& n, int per_sm) {
   c[n++] = {stage_launch_v<P, LS, DAG, BLK, POST, MINB, G>,
@@ -59,20 +61,31 @@ static void stage_cand(StageCand* c, int& n, int per_sm) {
 }
 template <int P, int LS, bool DAG, bool BLK, int POST>
 static void stage_cands(StageCand* c, int& n) {
-  if constexpr (P == P16 || P == PB16) {
+  constexpr bool H16 = (P == P16 || P == PB16);
+  if constexpr (POST == 1) {
+    // dense CUDA-core post: only where the recurrence is unstable or switched off
+    stage_cand<P, LS, DAG, BLK, POST, 2, H16 ? G_RING_CA : G_REG>(c, n, 0);
+  } else if constexpr (POST == 2) {
+    // tensor-core post: TMEM and the B operands are set up once per CTA, so a persistent
+    // grid pays off
     stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CG>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CG>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 3);
+  } else if constexpr (H16) {
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_BPF>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_BPF>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
     stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 3);
   } else if constexpr (P == P32) {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_PF>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_PF>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF_L>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF_LS>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF_LS>(c, n, 2);
   } else {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);
@@ -103,14 +116,16 @@ static cudaError_t stage_launch_one(const StageArgs& a, cudaStream_t st) {
     stage_cands<P, LS, DAG, BLK, 3>(c, n);
   } else if (H16 && a.post_h && a.post_struct == 2) {
     kind = 5;
-    stage_cands<P, LS, DAG, BLK, 2>(c, n);
-    stage_cands<P, LS, DAG, BLK, 4>(c, n);
+    if constexpr (H16) {
+      stage_cands<P, LS, DAG, BLK, 2>(c, n);
+      stage_cands<P, LS, DAG, BLK, 4>(c, n);
+    }
   } else if (a.post_struct) {
     kind = 4;
     stage_cands<P, LS, DAG, BLK, 4>(c, n);
   } else if (H16 && a.post_h) {
     kind = 2;
-    stage_cands<P, LS, DAG, BLK, 2>(c, n);
+    if constexpr (H16) stage_cands<P, LS, DAG, BLK, 2>(c, n);
   } else {
     kind = 1;
     stage_cands<P, LS, DAG, BLK, 1>(c, n);
