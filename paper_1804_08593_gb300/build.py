@@ -40,15 +40,17 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list | None = N
     """Compiles every csrc/*.cu and links lib/libdwf.so; returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    # stage_ls.cu is compiled once per (storage precision, Ls): its kernel variants dominate
+    # stage_ls.cu is compiled once per (storage precision, Ls, dag): its kernel variants dominate
     # the build, and the split lets them compile in parallel
     units = []
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         if os.path.basename(src) == "stage_ls.cu":
             for p in STAGE_PRECS:
                 for ls in STAGE_LS:
-                    units.append((src, [f"-DDWF_STAGE_P={p}", f"-DDWF_STAGE_LS={ls}"],
-                                  f"stage_p{p}_ls{ls}.o"))
+                    for dag in (0, 1):
+                        units.append((src, [f"-DDWF_STAGE_P={p}", f"-DDWF_STAGE_LS={ls}",
+                                            f"-DDWF_STAGE_DAG={dag}"],
+                                      f"stage_p{p}_ls{ls}_d{dag}.o"))
         else:
             units.append((src, [], os.path.basename(src)[:-3] + ".o"))
     # the longest units first

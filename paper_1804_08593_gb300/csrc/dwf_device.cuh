@@ -163,7 +163,14 @@ __device__ __forceinline__ void store_spinor(void* base, long Vp, long site, int
 }
 
 // The 9 complex elements of one link (16-byte vector loads).
-template <int P>
+// read-only load: through the non-coherent path from global memory, or plain from shared
+template <bool SMEM, typename T>
+__device__ __forceinline__ T ldro(const T* p) {
+  if constexpr (SMEM) return *p; else return __ldg(p);
+}
+
+// SMEM: base is the tile's links staged in shared memory ([dir][chunk][32 sites]).
+template <int P, bool SMEM = false>
 __device__ __forceinline__ void load_link9(cx<typename Prec<P>::acc> (&u)[9], const void* base,
                                            long Vp, long site, int dir) {
   constexpr int NCHL = Prec<P>::NCHL;
@@ -171,30 +178,30 @@ __device__ __forceinline__ void load_link9(cx<typename Prec<P>::acc> (&u)[9], co
   if constexpr (P == P64) {
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-      const double2 v = __ldg(reinterpret_cast<const double2*>(p + k * Vp));
+      const double2 v = ldro<SMEM>(reinterpret_cast<const double2*>(p + k * Vp));
       u[k] = {v.x, v.y};
     }
   } else if constexpr (P == P32) {
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-      const float4 v = __ldg(reinterpret_cast<const float4*>(p + k * Vp));
+      const float4 v = ldro<SMEM>(reinterpret_cast<const float4*>(p + k * Vp));
       u[2 * k] = {v.x, v.y};
       u[2 * k + 1] = {v.z, v.w};
     }
-    const float2 v = __ldg(reinterpret_cast<const float2*>(p + 4 * Vp));
+    const float2 v = ldro<SMEM>(reinterpret_cast<const float2*>(p + 4 * Vp));
     u[8] = {v.x, v.y};
   } else {
     constexpr bool BF = (P == PB16);
 #pragma unroll
     for (int k = 0; k < 2; k++) {
-      const uint4 v = __ldg(p + k * Vp);
+      const uint4 v = ldro<SMEM>(p + k * Vp);
       float2 a = h2f(v.x, BF), b = h2f(v.y, BF), c = h2f(v.z, BF), d = h2f(v.w, BF);
       u[4 * k] = {a.x, a.y};
       u[4 * k + 1] = {b.x, b.y};
       u[4 * k + 2] = {c.x, c.y};
       u[4 * k + 3] = {d.x, d.y};
     }
-    const float2 a = h2f(__ldg(reinterpret_cast<const unsigned int*>(p + 2 * Vp)), BF);
+    const float2 a = h2f(ldro<SMEM>(reinterpret_cast<const unsigned int*>(p + 2 * Vp)), BF);
     u[8] = {a.x, a.y};
   }
 }
@@ -222,7 +229,7 @@ template <typename A> __device__ __forceinline__ void zero(Spinor<A>& s) {
 // spins are sgn * B^dag times the projected upper half-spinor h = psi_up + sgn*B psi_dn.
 // B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.
 // ---------------------------------------------------------------------------------------
-template <int P, int MU>
+template <int P, int MU, bool SMEM = false>
 __device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
                                          const Spinor<typename Prec<P>::acc>& psi,
                                          const void* links, long Vp, long site, int dir,
@@ -250,7 +257,7 @@ __device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
     h[1][a] = {p1.x + sgn * b1.x, p1.y + sgn * b1.y};
   }
   cx<A> u[9];
-  load_link9<P>(u, links, Vp, site, dir);
+  load_link9<P, SMEM>(u, links, Vp, site, dir);
   cx<A> g[2][3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {

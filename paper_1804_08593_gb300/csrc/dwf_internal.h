@@ -217,9 +217,9 @@ dwf_status pack_full(dwf_ctx* h, Layout* lay, const void* src_c128, void* dst_ev
 dwf_status unpack_full(dwf_ctx* h, Layout* lay, const void* src_even, const void* src_odd,
                        int prec, void* dst_c128);
 
-// ---- stage kernels (stage_ls.cu per precision and Ls, stage_dispatch.cu) ----
-template <int P, int LS>
-cudaError_t stage_dispatch_ls(const StageArgs& a, bool dag, bool blocked, cudaStream_t st);
+// ---- stage kernels (stage_ls.cu per precision, Ls and dag; stage_dispatch.cu) ----
+template <int P, int LS, bool DAG>
+cudaError_t stage_dispatch_ls(const StageArgs& a, bool blocked, cudaStream_t st);
 cudaError_t launch_stage_prec(int prec, const StageArgs& a, int Ls, bool dag, bool blocked,
                               cudaStream_t st);
 

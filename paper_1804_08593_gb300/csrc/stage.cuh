@@ -30,7 +30,6 @@ struct StageArgs {
   const void* in;        // hop input, parity 1-p
   const void* in_halo;   // hop input for NBR_HALO neighbours (exact block operator)
   long Vp_in, Vp_halo;   // site strides of in / in_halo
-  const int* link_site;  // nullable: links of output site i are at link_site[i]
   long Vp_link;          // site stride of the link array
   int skip_halo;         // treat NBR_HALO neighbours as absent
   void* out;             // output, parity p (EPI_STORE / EPI_NORM)
@@ -88,11 +87,11 @@ inline void finish_stage_args(StageArgs& a, int Ls) {
 // 16-bit storage: the neighbour's spinor and the link stay packed in registers (12 + 12
 // 32-bit words) and each element is converted to FP32 where it is used, which keeps the
 // kernel's register footprint low enough for more resident CTAs per SM.
-template <int P, int MU>
+template <int P, int MU, bool SMEM = false>
 __device__ __forceinline__ void hop_term16(Spinor<float>& acc, const uint4 (&q)[3],
                                            const uint4* lp, long Vl, float sgn) {
   constexpr bool BF = (P == PB16);
-  const uint4 l0 = __ldg(lp), l1 = __ldg(lp + Vl), l2 = __ldg(lp + 2 * Vl);
+  const uint4 l0 = ldro<SMEM>(lp), l1 = ldro<SMEM>(lp + Vl), l2 = ldro<SMEM>(lp + 2 * Vl);
   auto sp = [&](int k) -> cx<float> {
     const uint4& w = q[k >> 2];
     const uint32_t v = (k & 3) == 0 ? w.x : (k & 3) == 1 ? w.y : (k & 3) == 2 ? w.z : w.w;
@@ -164,8 +163,31 @@ __device__ __forceinline__ void hop_term16(Spinor<float>& acc, const uint4 (&q)[
 // will read: everything (its links, the local-term and residual inputs, the 8 x Ls x chunk runs
 // of neighbour spinors), the links and streamed inputs, or the links only; so no direction
 // waits on DRAM for its links.  G_RING_BPF: links and streams in front of the L1-cached ring.
+// G_BPF_NX / G_RING_NX (persistent grids): prefetch the links and streamed inputs of the
+// CTA's NEXT tile while this one is computed (and this tile's on the CTA's first tile).
+// G_TMA / G_RING_TMA: the tile's links are copied into shared memory by the TMA engine (one
+// cp.async.bulk per 512-byte run, completing on an mbarrier) and every warp reads them from
+// there; neighbours into registers, or through the ring.
 enum Gather { G_REG = 0, G_RING_CA = 1, G_PF = 2, G_RING_CG = 3, G_BPF = 4, G_RING_BPF = 5,
-              G_BPF_LS = 6, G_BPF_L = 7 };
+              G_BPF_LS = 6, G_BPF_L = 7, G_BPF_NX = 8, G_RING_NX = 9, G_TMA = 10,
+              G_RING_TMA = 11 };
+__host__ __device__ constexpr bool gather_ring(int g) {
+  return g == G_RING_CA || g == G_RING_CG || g == G_RING_BPF || g == G_RING_NX ||
+         g == G_RING_TMA;
+}
+__host__ __device__ constexpr bool gather_tma(int g) { return g == G_TMA || g == G_RING_TMA; }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(tc::smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy by the TMA engine; completes `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :: "r"(tc::smem_u32(dst)), "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar)) : "memory");
+}
 // bulk-prefetch depth of a gather mode (0: none)
 __host__ __device__ constexpr int bpf_what(int g) {
   return g == G_BPF ? 3 : g == G_BPF_LS ? 2 : g == G_BPF_L ? 1 : g == G_RING_BPF ? 2 : 0;
@@ -238,9 +260,11 @@ __device__ __forceinline__ void prefetch_nbr(const StageArgs& a, uint32_t nb, in
   for (int k = 0; k < NCH; k++) asm volatile("prefetch.global.L1 [%0];" :: "l"(p + k * vs));
 }
 
-template <int P, int D, bool DAG, bool BLOCKED>
+// LSM: links from the tile's shared-memory copy lsm ([dir][chunk][32]; lsite = lane)
+template <int P, int D, bool DAG, bool BLOCKED, bool LSM = false>
 __device__ __forceinline__ void hop_dir_nb(Spinor<typename Prec<P>::acc>& acc,
-                                           const StageArgs& a, uint32_t nb, long lsite, int s) {
+                                           const StageArgs& a, uint32_t nb, long lsite, int s,
+                                           const void* lsm = nullptr) {
   using A = typename Prec<P>::acc;
   const void* src;
   long vs;
@@ -249,22 +273,26 @@ __device__ __forceinline__ void hop_dir_nb(Spinor<typename Prec<P>::acc>& acc,
   // forward hop: (1 - gamma_mu), backward: (1 + gamma_mu); the adjoint swaps them.
   constexpr bool back = (D & 1) != 0;
   const A sgn = (back != DAG) ? A(1) : A(-1);
+  const void* lb = LSM ? lsm : a.links;
+  const long vl = LSM ? 32 : a.Vp_link;
   if constexpr (P == P16 || P == PB16) {
     const uint4* p = reinterpret_cast<const uint4*>(src) + ((long)s * 3) * vs + j;
     const uint4 q[3] = {__ldg(p), __ldg(p + vs), __ldg(p + 2 * vs)};
-    const uint4* lp = reinterpret_cast<const uint4*>(a.links) + (long)D * 3 * a.Vp_link + lsite;
-    hop_term16<P, D / 2>(acc, q, lp, a.Vp_link, sgn);
+    const uint4* lp = reinterpret_cast<const uint4*>(lb) + (long)D * 3 * vl + lsite;
+    hop_term16<P, D / 2, LSM>(acc, q, lp, vl, sgn);
   } else {
     Spinor<A> psi;
     load_spinor<P>(psi, src, vs, j, s);
-    hop_term<P, D / 2>(acc, psi, a.links, a.Vp_link, lsite, D, sgn);
+    hop_term<P, D / 2, LSM>(acc, psi, lb, vl, lsite, D, sgn);
   }
 }
 
-template <int P, int D, bool DAG, bool BLOCKED>
+template <int P, int D, bool DAG, bool BLOCKED, bool LSM = false>
 __device__ __forceinline__ void hop_dir(Spinor<typename Prec<P>::acc>& acc, const StageArgs& a,
-                                        long site, long lsite, int s) {
-  hop_dir_nb<P, D, DAG, BLOCKED>(acc, a, __ldg(a.nbr + (long)D * a.Vp + site), lsite, s);
+                                        long site, long lsite, int s,
+                                        const void* lsm = nullptr) {
+  hop_dir_nb<P, D, DAG, BLOCKED, LSM>(acc, a, __ldg(a.nbr + (long)D * a.Vp + site), lsite, s,
+                                      lsm);
 }
 
 // FP32 and 16-bit stages: the eight neighbour spinors are gathered with cp.async into a
@@ -296,13 +324,14 @@ __host__ __device__ constexpr size_t ring_bytes(int Ls) {
   return (P == P16 || P == PB16 || P == P32) ? (size_t)2 * Prec<P>::NCH * 32 * Ls * 16 : 0;
 }
 
-template <int P, bool DAG, bool BLOCKED, bool L1>
+template <int P, bool DAG, bool BLOCKED, bool L1, bool LSM = false>
 struct HopRing {
   static constexpr int NC = Prec<P>::NCH;
   const StageArgs& a;
   long site, lsite;
   int s, tid, nt;
   uint4* ring;          // [2][NC][nt] uint4
+  const uint4* lsm;     // LSM: the tile's links in shared memory (lsite = lane)
   uint32_t nb[8];
   __device__ __forceinline__ bool present(int d) const {
     if constexpr (BLOCKED) {
@@ -346,8 +375,10 @@ struct HopRing {
       hop_term<P, D / 2>(acc, psi, a.links, a.Vp_link, lsite, D, sgn);
     } else {
       const uint4 q[3] = {slot[0], slot[nt], slot[2 * nt]};
-      const uint4* lp = reinterpret_cast<const uint4*>(a.links) + (long)D * 3 * a.Vp_link + lsite;
-      hop_term16<P, D / 2>(acc, q, lp, a.Vp_link, sgn);
+      const long vl = LSM ? 32 : a.Vp_link;
+      const uint4* lp = (LSM ? lsm : reinterpret_cast<const uint4*>(a.links)) + (long)D * 3 * vl +
+                        lsite;
+      hop_term16<P, D / 2, LSM>(acc, q, lp, vl, sgn);
     }
   }
   template <int D>
@@ -473,6 +504,22 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
   }
 }
 
+// Dynamic shared memory of a stage: the gather ring or the post matrices' staging area.
+template <int P>
+__host__ __device__ constexpr size_t stage_smem_base(int Ls, int post, int gather) {
+  const size_t ring = gather_ring(gather) ? ring_bytes<P>(Ls) : 0;
+  size_t need = 0;
+  if (post == 1) need = (size_t)(Ls * 24 * 32 + 2 * Ls * Ls) * sizeof(typename Prec<P>::acc);
+  if (post == 3 || post == 4) need = (size_t)Ls * 24 * 32 * sizeof(typename Prec<P>::acc);
+  if (post == 2) need = tc_offset(Ls) + 6 * tc::TILE_BYTES + 2 * tc::B_BYTES;
+  return need > ring ? need : ring;
+}
+
+// TMA link staging: the tile's 8 x NCHL link runs of 512 bytes after the ring / post area
+template <int P>
+__host__ __device__ constexpr size_t tma_link_offset(int Ls, int post, int gather) {
+  return (stage_smem_base<P>(Ls, post, gather) + 127) / 128 * 128;
+}
 // POST: 0 = no post matrix, 1 = CUDA-core column GEMM, 2 = tensor cores (16-bit only),
 //       3 = D+^dag applied sparsely (b + c K^dag: neighbours in s through shared memory),
 //       4 = D+ M5op^-1 (dag: M5op^-dag D+^dag) by an O(Ls) recurrence per column
@@ -480,7 +527,8 @@ template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
                                            unsigned char* smem_raw, double* red_scratch,
                                            uint64_t* tc_mbar, uint32_t* tc_slot,
-                                           uint32_t& tc_phase) {
+                                           uint32_t& tc_phase, uint64_t* lk_mbar,
+                                           uint32_t& lk_phase) {
   using A = typename Prec<P>::acc;
   const int lane = threadIdx.x, s = threadIdx.y;
   const int tid = lane + 32 * s;
@@ -513,20 +561,52 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
 
   Spinor<A> acc;
   zero(acc);
-  if constexpr (G == G_RING_CA || G == G_RING_CG || G == G_RING_BPF) {
+  // G_TMA / G_RING_TMA: stage the tile's links in shared memory (after the ring / post area)
+  const uint4* lsm = nullptr;
+  if constexpr (gather_tma(G)) {
+    constexpr int NCHL = Prec<P>::NCHL;
+    unsigned char* lk = smem_raw + tma_link_offset<P>(LS, POST, G);
+    if (tid == 0) {
+      tc::fence_proxy_async_smem();   // earlier generic reads of the buffer come first
+      mbar_expect_tx(lk_mbar, 8 * NCHL * 512);
+      const uint4* L = reinterpret_cast<const uint4*>(a.links);
+      for (int i = 0; i < 8 * NCHL; i++)
+        bulk_g2s(lk + i * 512, L + (long)i * a.Vp_link + tile * 32, 512, lk_mbar);
+    }
+    if (!tc::mbar_wait(lk_mbar, lk_phase) && a.err) atomicExch(a.err, 1);
+    lk_phase ^= 1u;
+    lsm = reinterpret_cast<const uint4*>(lk);
+  }
+  if constexpr (G == G_BPF_NX || G == G_RING_NX) {
+    if (tile < (long)gridDim.x) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
+    if (tile + (long)gridDim.x < a.ntiles) prefetch_tile<P, LS, BLOCKED, 2>(a, tile + gridDim.x);
+  }
+  if constexpr (gather_ring(G)) {
     if constexpr (G == G_RING_BPF) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
     if (valid) {
-      const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
-      HopRing<P, DAG, BLOCKED, G != G_RING_CG> hp{a, site, lsite, s, tid, NT,
-                                                  reinterpret_cast<uint4*>(smem_raw)};
+      const long lsite = site;
+      constexpr bool LSM = gather_tma(G);
+      HopRing<P, DAG, BLOCKED, G != G_RING_CG, LSM> hp{
+          a, site, LSM ? (long)lane : lsite, s, tid, NT, reinterpret_cast<uint4*>(smem_raw), lsm};
       hp.run(acc);
     }
     // the post stage reuses shared memory that other threads' rings occupy
     __syncthreads();
-  } else if (G == G_BPF || G == G_BPF_LS || G == G_BPF_L) {
-    prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
+  } else if (G == G_TMA) {
     if (valid) {
-      const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
+      hop_dir<P, 0, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+      hop_dir<P, 1, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+      hop_dir<P, 2, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+      hop_dir<P, 3, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+      hop_dir<P, 4, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+      hop_dir<P, 5, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+      hop_dir<P, 6, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+      hop_dir<P, 7, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+    }
+  } else if (G == G_BPF || G == G_BPF_LS || G == G_BPF_L || G == G_BPF_NX) {
+    if constexpr (G != G_BPF_NX) prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
+    if (valid) {
+      const long lsite = site;
       hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
       hop_dir<P, 1, DAG, BLOCKED>(acc, a, site, lsite, s);
       hop_dir<P, 2, DAG, BLOCKED>(acc, a, site, lsite, s);
@@ -538,7 +618,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
   } else if (G == G_PF) {
     if (valid) {
-      const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
+      const long lsite = site;
       uint32_t nb[8];
 #pragma unroll
       for (int d = 0; d < 8; d++) nb[d] = __ldg(a.nbr + (long)d * a.Vp + site);
@@ -560,7 +640,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       hop_dir_nb<P, 7, DAG, BLOCKED>(acc, a, nb[7], lsite, s);
     }
   } else if (valid) {
-    const long lsite = a.link_site ? (long)__ldg(a.link_site + site) : site;
+    const long lsite = site;
     hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
     hop_dir<P, 1, DAG, BLOCKED>(acc, a, site, lsite, s);
     hop_dir<P, 2, DAG, BLOCKED>(acc, a, site, lsite, s);
@@ -778,10 +858,15 @@ __global__ void __launch_bounds__(32 * LS, MINB) stage_kernel(const StageArgs a)
   __shared__ uint32_t tc_slot;
   constexpr bool TC = (POST == 2 && (P == P16 || P == PB16));
   if constexpr (TC) tc_setup<LS>(a, smem_raw, &tc_mbar, &tc_slot);
-  uint32_t tc_phase = 0;
+  __shared__ uint64_t lk_mbar;
+  if constexpr (gather_tma(G)) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) tc::mbar_init(&lk_mbar, 1);
+    __syncthreads();
+  }
+  uint32_t tc_phase = 0, lk_phase = 0;
   for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     stage_tile<P, LS, DAG, BLOCKED, POST, G>(a, tile, smem_raw, red_scratch, &tc_mbar,
-                                             &tc_slot, tc_phase);
+                                             &tc_slot, tc_phase, &lk_mbar, lk_phase);
     __syncthreads();
   }
   if constexpr (TC) tc_teardown(&tc_slot);
@@ -789,13 +874,9 @@ __global__ void __launch_bounds__(32 * LS, MINB) stage_kernel(const StageArgs a)
 
 template <int P>
 size_t stage_smem_bytes(int Ls, int post, int gather) {
-  const size_t ring =
-      (gather == G_RING_CA || gather == G_RING_CG || gather == G_RING_BPF) ? ring_bytes<P>(Ls) : 0;
-  size_t need = 0;
-  if (post == 1) need = (size_t)(Ls * 24 * 32 + 2 * Ls * Ls) * sizeof(typename Prec<P>::acc);
-  if (post == 3 || post == 4) need = (size_t)Ls * 24 * 32 * sizeof(typename Prec<P>::acc);
-  if (post == 2) need = tc_offset(Ls) + 6 * tc::TILE_BYTES + 2 * tc::B_BYTES;
-  return need > ring ? need : ring;
+  if (gather_tma(gather))
+    return tma_link_offset<P>(Ls, post, gather) + (size_t)8 * Prec<P>::NCHL * 512;
+  return stage_smem_base<P>(Ls, post, gather);
 }
 
 }  // namespace dwf

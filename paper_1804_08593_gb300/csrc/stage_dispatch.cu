@@ -5,18 +5,24 @@
 
 namespace dwf {
 
+template <int P, bool DAG>
+static cudaError_t launch_stage_pd(const StageArgs& a, int Ls, bool blocked, cudaStream_t st) {
+  switch (Ls) {
+    case 4: return stage_dispatch_ls<P, 4, DAG>(a, blocked, st);
+    case 6: return stage_dispatch_ls<P, 6, DAG>(a, blocked, st);
+    case 8: return stage_dispatch_ls<P, 8, DAG>(a, blocked, st);
+    case 10: return stage_dispatch_ls<P, 10, DAG>(a, blocked, st);
+    case 12: return stage_dispatch_ls<P, 12, DAG>(a, blocked, st);
+    case 16: return stage_dispatch_ls<P, 16, DAG>(a, blocked, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int P>
 static cudaError_t launch_stage_p(const StageArgs& a, int Ls, bool dag, bool blocked,
                                   cudaStream_t st) {
-  switch (Ls) {
-    case 4: return stage_dispatch_ls<P, 4>(a, dag, blocked, st);
-    case 6: return stage_dispatch_ls<P, 6>(a, dag, blocked, st);
-    case 8: return stage_dispatch_ls<P, 8>(a, dag, blocked, st);
-    case 10: return stage_dispatch_ls<P, 10>(a, dag, blocked, st);
-    case 12: return stage_dispatch_ls<P, 12>(a, dag, blocked, st);
-    case 16: return stage_dispatch_ls<P, 16>(a, dag, blocked, st);
-    default: return cudaErrorInvalidValue;
-  }
+  return dag ? launch_stage_pd<P, true>(a, Ls, blocked, st)
+             : launch_stage_pd<P, false>(a, Ls, blocked, st);
 }
 
 cudaError_t launch_stage_prec(int prec, const StageArgs& args, int Ls, bool dag, bool blocked,

@@ -47,13 +47,14 @@ struct StageTune {
   bool pending = false;
 };
 
-// The variants timed per stage kind.  FP32 gathers into registers, plain or after a bulk L2
-// prefetch of the tile's links (and streamed inputs, and neighbour runs), as one CTA per tile
-// or a persistent grid of 2 CTAs per SM
-// (a register budget for 3 CTAs per SM spills; the cp.async ring and per-direction L1
-// prefetch measured slower and were dropped).  FP16/BF16 gather through the L1-cached
-// cp.async ring, with a register budget for 2 or 3 CTAs per SM, with or without the bulk
-// prefetch, or persistent.  FP64 (ALU bound): one CTA per tile or persistent.
+// The variants timed per stage kind (the first is the default for launches that are never
+// timed).  FP32 gathers into registers, plain or after a bulk L2 prefetch of the tile's links
+// (and streamed inputs), or with the tile's links copied into shared memory by the TMA engine;
+// a register budget for 3 CTAs per SM spills, and the cp.async ring, per-direction L1
+// prefetch, prefetching the neighbour runs and prefetching the next tile of a persistent CTA
+// measured slower.  FP16/BF16 gather through the L1-cached cp.async ring with a register
+// budget for 2 or 3 CTAs per SM, with the tile's links and streams prefetched into L2 or its
+// links staged in shared memory by TMA.  FP64 (ALU bound): one CTA per tile or persistent.
 template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G>
 static void stage_cand(StageCand* c, int& n, int per_sm) {
   c[n++] = {stage_launch_v<P, LS, DAG, BLK, POST, MINB, G>,
@@ -73,19 +74,18 @@ static void stage_cands(StageCand* c, int& n) {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
     stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 3);
   } else if constexpr (H16) {
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_BPF>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_BPF>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
-    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 3);
+    // up to Ls = 12 a budget for 3 CTAs per SM (56 registers) wins; beyond, it spills
+    constexpr int MB = LS <= 12 ? 3 : 2;
+    stage_cand<P, LS, DAG, BLK, POST, MB, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 5 - MB, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, MB, G_RING_BPF>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, MB, G_RING_TMA>(c, n, 0);
   } else if constexpr (P == P32) {
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF_L>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF_LS>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF_LS>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA>(c, n, 2);
   } else {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);
@@ -198,13 +198,10 @@ static cudaError_t stage_launch_one(const StageArgs& a, cudaStream_t st) {
   return c[v].fn(b, c[v].smem, grid_of(c[v]), st);
 }
 
-template <int P, int LS>
-cudaError_t stage_dispatch_ls(const StageArgs& a, bool dag, bool blocked, cudaStream_t st) {
-  if (dag)
-    return blocked ? stage_launch_one<P, LS, true, true>(a, st)
-                   : stage_launch_one<P, LS, true, false>(a, st);
-  return blocked ? stage_launch_one<P, LS, false, true>(a, st)
-                 : stage_launch_one<P, LS, false, false>(a, st);
+template <int P, int LS, bool DAG>
+cudaError_t stage_dispatch_ls(const StageArgs& a, bool blocked, cudaStream_t st) {
+  return blocked ? stage_launch_one<P, LS, DAG, true>(a, st)
+                 : stage_launch_one<P, LS, DAG, false>(a, st);
 }
 
 }  // namespace dwf
