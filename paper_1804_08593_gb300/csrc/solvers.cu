@@ -7,11 +7,21 @@
 //     CG in FP32 (FP64 reliable updates) or FP64.
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "engine.h"
 
 namespace dwf {
+
+// Reliable updates: the low-precision iteration hands its iterate to the FP64 solution and
+// restarts from the FP64 true residual b - A x once its own residual has dropped by delta
+// (DWF_RU_DELTA overrides 0.1; values outside (0, 1) are ignored).
+static double ru_delta() {
+  const char* e = getenv("DWF_RU_DELTA");
+  const double d = e ? atof(e) : 0.1;
+  return (d > 0.0 && d < 1.0) ? d : 0.1;
+}
 
 // Device scalar slots of one solve.
 enum Slot {
@@ -239,7 +249,7 @@ static dwf_status run_cg(dwf_ctx* h, Layout* lay, const void* b_c128, void* x_c1
   DWF_TRY(true_residual(E64, b64, x0 ? x64 : nullptr, r64, t1, t2, t3, dsc, &rr));
   if (stats) stats->operator_applications += x0 ? 1 : 0;
 
-  const double delta = (prec == P64) ? 0.0 : 0.1;
+  const double delta = (prec == P64) ? 0.0 : ru_delta();
   const bool scaled = (prec == P16 || prec == PB16);
   const double nreal = 24.0 * h->Ls * (double)(g.V / 2);
   const double tol2 = tol * tol * bb;
@@ -532,7 +542,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   }
   rr64 = bb;
   const double tol2 = tol * tol * bb;
-  const double delta = (middle == P64) ? 0.0 : 0.1;
+  const double delta = (middle == P64) ? 0.0 : ru_delta();
   const int nbk = gb.nblocks;
 
   DWF_TRY(cast(Em, P64, r64, rm, 1.0, nullptr, 0, nullptr, Em.red(FIN_STORE, dsc + S_RR)));

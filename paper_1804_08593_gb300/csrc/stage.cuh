@@ -163,17 +163,13 @@ __device__ __forceinline__ void hop_term16(Spinor<float>& acc, const uint4 (&q)[
 // will read: everything (its links, the local-term and residual inputs, the 8 x Ls x chunk runs
 // of neighbour spinors), the links and streamed inputs, or the links only; so no direction
 // waits on DRAM for its links.  G_RING_BPF: links and streams in front of the L1-cached ring.
-// G_BPF_NX / G_RING_NX (persistent grids): prefetch the links and streamed inputs of the
-// CTA's NEXT tile while this one is computed (and this tile's on the CTA's first tile).
 // G_TMA / G_RING_TMA: the tile's links are copied into shared memory by the TMA engine (one
 // cp.async.bulk per 512-byte run, completing on an mbarrier) and every warp reads them from
 // there; neighbours into registers, or through the ring.
 enum Gather { G_REG = 0, G_RING_CA = 1, G_PF = 2, G_RING_CG = 3, G_BPF = 4, G_RING_BPF = 5,
-              G_BPF_LS = 6, G_BPF_L = 7, G_BPF_NX = 8, G_RING_NX = 9, G_TMA = 10,
-              G_RING_TMA = 11 };
+              G_BPF_LS = 6, G_BPF_L = 7, G_TMA = 10, G_RING_TMA = 11 };
 __host__ __device__ constexpr bool gather_ring(int g) {
-  return g == G_RING_CA || g == G_RING_CG || g == G_RING_BPF || g == G_RING_NX ||
-         g == G_RING_TMA;
+  return g == G_RING_CA || g == G_RING_CG || g == G_RING_BPF || g == G_RING_TMA;
 }
 __host__ __device__ constexpr bool gather_tma(int g) { return g == G_TMA || g == G_RING_TMA; }
 
@@ -577,10 +573,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     lk_phase ^= 1u;
     lsm = reinterpret_cast<const uint4*>(lk);
   }
-  if constexpr (G == G_BPF_NX || G == G_RING_NX) {
-    if (tile < (long)gridDim.x) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
-    if (tile + (long)gridDim.x < a.ntiles) prefetch_tile<P, LS, BLOCKED, 2>(a, tile + gridDim.x);
-  }
   if constexpr (gather_ring(G)) {
     if constexpr (G == G_RING_BPF) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
     if (valid) {
@@ -603,8 +595,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       hop_dir<P, 6, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
       hop_dir<P, 7, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
     }
-  } else if (G == G_BPF || G == G_BPF_LS || G == G_BPF_L || G == G_BPF_NX) {
-    if constexpr (G != G_BPF_NX) prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
+  } else if (G == G_BPF || G == G_BPF_LS || G == G_BPF_L) {
+    prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
     if (valid) {
       const long lsite = site;
       hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);

@@ -37,11 +37,13 @@ def test_force_matches_oracle(prm):
     assert abs(S - So) <= 1e-12 * abs(So)
 
 
-def test_force_central_differences_8x8x8x16():
-    """Moebius 8^3x16 x Ls=8 (mf = 0.02, eps = 0.3, seed 5): analytic gradient vs central
-    differences of the action along 20 random su(3) directions, all links at once."""
+@pytest.mark.parametrize("name", ["mobius_8x8x8x16_ls8", "mobius_16x16x16x16_ls16"])
+def test_force_central_differences(name):
+    """Moebius 8^3x16 x Ls=8 and 16^4 x Ls=16 (mf = 0.02, eps = 0.3, seed 5): analytic gradient
+    vs FP64 central differences of the action (stationary estimator, solves to 1e-13) along 20
+    random su(3) directions, all links at once."""
     dwf = lib()
-    w = inputs.workload("mobius_8x8x8x16_ls8")
+    w = inputs.workload(name)
     p = o.DWFParams(w["dims"], w["Ls"], w["M5"], w["mf"], w["b"], w["c"])
     U, phi = w["links"], w["phi"]
     h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
