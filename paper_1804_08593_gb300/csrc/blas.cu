@@ -26,7 +26,7 @@ __device__ __forceinline__ bool last_cta(unsigned* counter, unsigned total) {
 template <int P, int LS>
 __global__ void __launch_bounds__(32 * LS) vec_kernel(const VecArgs a) {
   using A = typename Prec<P>::acc;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x, s = threadIdx.y;
   const long site = (long)blockIdx.x * 32 + lane;
   int seg;
@@ -194,8 +194,38 @@ __global__ void cast_kernel(const CastArgs a) {
   for (int k = 0; k < 12; k++) w.c[k] = {AO((AW)v.c[k].x * f), AO((AW)v.c[k].y * f)};
   store_spinor<PO>(a.out, a.Vp, site, s, w);
   if (a.out2) store_spinor<PO>(a.out2, a.Vp, site, s, w);
+  round_to_storage<PO>(w);   // from here on: the values as stored
+  if (a.out3) {
+    // u_s = db w_s + dc (P- w_{s+1} + P+ w_{s-1}),  w_{Ls} = -mf w_0, w_{-1} = -mf w_{Ls-1}:
+    // the slices of the site are the CTA's other warps, exchanged through shared memory
+    extern __shared__ __align__(128) unsigned char cast_smem[];
+    AO* buf = reinterpret_cast<AO*>(cast_smem);
+    const int Ls = blockDim.y;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      buf[(s * 24 + 2 * k) * 32 + lane] = w.c[k].x;
+      buf[(s * 24 + 2 * k + 1) * 32 + lane] = w.c[k].y;
+    }
+    __syncthreads();
+    AO db, dc, mf;
+    if constexpr (sizeof(AO) == 8) {
+      db = a.db; dc = a.dc; mf = a.mf;
+    } else {
+      db = a.dbf; dc = a.dcf; mf = a.mff;
+    }
+    const int su = s + 1 < Ls ? s + 1 : 0, sd = s > 0 ? s - 1 : Ls - 1;
+    const AO fu = (s + 1 < Ls) ? AO(1) : -mf, fd = (s > 0) ? AO(1) : -mf;
+    Spinor<AO> u;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const int sn = k < 6 ? sd : su;
+      const AO f = k < 6 ? fd : fu;
+      u.c[k].x = db * w.c[k].x + dc * f * buf[(sn * 24 + 2 * k) * 32 + lane];
+      u.c[k].y = db * w.c[k].y + dc * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+    }
+    store_spinor<PO>(a.out3, a.Vp, site, s, u);
+  }
   if (a.red.partial) {
-    round_to_storage<PO>(w);
     AO part = AO(0);
     if (a.dotv) {
       Spinor<AO> d;
@@ -215,15 +245,30 @@ __global__ void cast_kernel(const CastArgs a) {
   }
 }
 
+template <int PI, int PO>
+static cudaError_t cast_go(const CastArgs& a, dim3 g, dim3 b, cudaStream_t st) {
+  using AO = typename Prec<PO>::acc;
+  static bool attr = false;
+  if (!attr) {   // room for the D+ exchange of the largest Ls
+    cudaError_t e = cudaFuncSetAttribute(cast_kernel<PI, PO>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(16 * 24 * 32 * sizeof(AO)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const size_t sm = a.out3 ? (size_t)b.y * 24 * 32 * sizeof(AO) : 0;
+  cast_kernel<PI, PO><<<g, b, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int PI>
 static cudaError_t cast_out(int pout, const CastArgs& a, dim3 g, dim3 b, cudaStream_t st) {
   switch (pout) {
-    case P64: cast_kernel<PI, P64><<<g, b, 0, st>>>(a); break;
-    case P32: cast_kernel<PI, P32><<<g, b, 0, st>>>(a); break;
-    case P16: cast_kernel<PI, P16><<<g, b, 0, st>>>(a); break;
-    default: cast_kernel<PI, PB16><<<g, b, 0, st>>>(a);
+    case P64: return cast_go<PI, P64>(a, g, b, st);
+    case P32: return cast_go<PI, P32>(a, g, b, st);
+    case P16: return cast_go<PI, P16>(a, g, b, st);
+    default: return cast_go<PI, PB16>(a, g, b, st);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_cast(int pin, int pout, const CastArgs& a, int Ls, cudaStream_t st) {
@@ -281,8 +326,8 @@ __global__ void vop_kernel(const VopArgs a) {
       Spinor<A> x;
       load_spinor<P>(x, a.x, a.Vp, site, s);
       load_spinor<P>(y, a.y, a.Vp, site, s);
-#pragma unroll
       A part = A(0);
+#pragma unroll
       for (int k = 0; k < 12; k++) {
         y.c[k].x = x.c[k].x - y.c[k].x;
         y.c[k].y = x.c[k].y - y.c[k].y;

@@ -260,6 +260,9 @@ struct CastArgs {
   int invert;            // use 1/f
   const void* dotv;      // nullable
   void* out2;            // nullable: second copy of out
+  void* out3;            // nullable: D+ out (Moebius pre-op of the stored out)
+  double db, dc, mf;     // D+ = db + dc K, walls -mf (out3)
+  float dbf, dcf, mff;   // the same in FP32
   const int* stop;
   RedArgs red;
   const int* tile_seg;   // batched mode (nullable)

@@ -59,14 +59,23 @@ static dwf_status vop(const OpEngine& E, int op, const void* x, void* y, RedArgs
 
 // out (Eout's layout and precision) = f * in, f = num or sqrt(num / *den) (inverted if asked);
 // in_map: in is in another site order (out site i reads in site in_map[i], stride vp_in)
+// out3: also u = D+ out (the Moebius pre-op of what was stored), in the same pass
 static dwf_status cast(const OpEngine& Eout, int pin, const void* in, void* out, double num,
                        const double* den, int invert, const void* dotv, RedArgs red,
-                       void* out2 = nullptr, const int* in_map = nullptr, long vp_in = 0) {
+                       void* out2 = nullptr, const int* in_map = nullptr, long vp_in = 0,
+                       void* out3 = nullptr) {
   CastArgs a{};
   a.in = in;
   a.out = out;
   a.in_map = in_map;
   a.Vp_in = vp_in;
+  a.out3 = out3;
+  a.db = Eout.h->b;
+  a.dc = Eout.h->c;
+  a.mf = Eout.h->mf;
+  a.dbf = (float)a.db;
+  a.dcf = (float)a.dc;
+  a.mff = (float)a.mf;
   a.Vp = Eout.g().Vp;
   a.Vhb = Eout.g().Vhb;
   a.Vhb_pad = Eout.g().Vhb_pad;
@@ -77,7 +86,8 @@ static dwf_status cast(const OpEngine& Eout, int pin, const void* in, void* out,
   a.out2 = out2;
   a.red = red;
   ProfScope ps(&Eout.h->prof, Eout.h->stream, "cast",
-               field_bytes(Eout.g(), pin) + field_bytes(Eout.g(), Eout.prec) * (out2 ? 2 : 1) +
+               field_bytes(Eout.g(), pin) +
+                   field_bytes(Eout.g(), Eout.prec) * (1 + (out2 ? 1 : 0) + (out3 ? 1 : 0)) +
                    (dotv ? field_bytes(Eout.g(), Eout.prec) : 0),
                0.0);
   DWF_CUDA(launch_cast(pin, Eout.prec, a, Eout.h->Ls, Eout.h->stream));
@@ -405,9 +415,8 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
   const bool remap = (Em.lay != Ei.lay);
   DWF_TRY(cast(Ei, Em.prec, r, iv.ri, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 0,
                nullptr, Ei.red(FIN_STORE, rho_b), iv.pi, remap ? Ei.lay->cb_even : nullptr,
-               Em.g().Vp));
+               Em.g().Vp, Ei.trivial() ? nullptr : iv.ui));
   DWF_TRY(vop(Ei, VOP_ZERO, nullptr, iv.xi));
-  if (!Ei.trivial()) DWF_TRY(Ei.dplus(iv.pi, iv.ui, nullptr));
   double* papx_b = blk + 4 * nb;
   for (int k = 0; k < l; k++) {
     // the last local iteration needs only ||Mpc p||^2 (for alpha), not Mpc p itself
