@@ -155,23 +155,27 @@ __device__ __forceinline__ void hop_term16(Spinor<float>& acc, const uint4 (&q)[
   }
 }
 
-// How a stage gathers the eight neighbour spinors (a launch-variant choice, timed by the
-// autotuner): straight into registers; through a two-slot cp.async ring in shared memory
-// (caching in L1, or in L2 only); or into registers with the indices loaded up front and
-// direction d+1 prefetched into L1 while direction d is computed.
-// G_BPF / G_BPF_LS / G_BPF_L: registers, after one bulk L2 prefetch per tile of what the tile
-// will read: everything (its links, the local-term and residual inputs, the 8 x Ls x chunk runs
-// of neighbour spinors), the links and streamed inputs, or the links only; so no direction
-// waits on DRAM for its links.  G_RING_BPF: links and streams in front of the L1-cached ring.
-// G_TMA / G_RING_TMA: the tile's links are copied into shared memory by the TMA engine (one
-// cp.async.bulk per 512-byte run, completing on an mbarrier) and every warp reads them from
-// there; neighbours into registers, or through the ring.
-enum Gather { G_REG = 0, G_RING_CA = 1, G_PF = 2, G_RING_CG = 3, G_BPF = 4, G_RING_BPF = 5,
-              G_BPF_LS = 6, G_BPF_L = 7, G_TMA = 10, G_RING_TMA = 11 };
+// How a stage gathers the eight neighbour spinors and its links (a launch-variant choice, timed
+// by the autotuner): neighbours straight into registers or through a two-slot cp.async ring in
+// shared memory; links from global memory after an optional bulk L2 prefetch of the tile's
+// links (G_BPF_L; G_BPF_LS / G_RING_BPF also prefetch the streamed inputs: local-term input,
+// residual), or copied into shared memory by the TMA engine (G_TMA / G_RING_TMA: one
+// cp.async.bulk per 512-byte run, completing on an mbarrier) and read by every warp from there.
+// Either way each tile's links come from DRAM once and no direction waits on DRAM for them.
+enum Gather { G_REG = 0, G_RING = 1, G_RING_BPF = 5, G_BPF_LS = 6, G_BPF_L = 7, G_TMA = 10,
+              G_RING_TMA = 11 };
 __host__ __device__ constexpr bool gather_ring(int g) {
-  return g == G_RING_CA || g == G_RING_CG || g == G_RING_BPF || g == G_RING_TMA;
+  return g == G_RING || g == G_RING_BPF || g == G_RING_TMA;
 }
 __host__ __device__ constexpr bool gather_tma(int g) { return g == G_TMA || g == G_RING_TMA; }
+// bulk-prefetch depth of a gather mode: 0 none, 1 links, 2 links and streamed inputs
+__host__ __device__ constexpr int bpf_what(int g) {
+  return g == G_BPF_LS ? 2 : g == G_BPF_L ? 1 : g == G_RING_BPF ? 2 : 0;
+}
+
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p), "r"(bytes) : "memory");
+}
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
@@ -184,21 +188,11 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       :: "r"(tc::smem_u32(dst)), "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar)) : "memory");
 }
-// bulk-prefetch depth of a gather mode (0: none)
-__host__ __device__ constexpr int bpf_what(int g) {
-  return g == G_BPF ? 3 : g == G_BPF_LS ? 2 : g == G_BPF_L ? 1 : g == G_RING_BPF ? 2 : 0;
-}
 
-__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p), "r"(bytes) : "memory");
-}
-
-// Every run is 32 sites x 16 bytes = 512 bytes starting at a site index in [0, Vp - 32]
-// (tiles cover [0, Vp); a neighbour run starts at the tile's first neighbour and is clamped to
-// the array).  WHAT: 1 the tile's links, 2 also its streamed inputs (local-term input,
-// residual), 3 also the neighbour runs (whole-lattice stages only: halo arrays have absent
-// neighbours).  A bulk prefetch takes warp-uniform operands, so lane 0 of each warp issues
-// its share (a per-lane loop would be serialised lane by lane).
+// Every run is 32 sites x 16 bytes = 512 bytes starting at the tile's first site (tiles cover
+// [0, Vp)).  WHAT: 1 the tile's links, 2 also its streamed inputs (local-term input, residual).
+// A bulk prefetch takes warp-uniform operands, so lane 0 of each warp issues its share (a
+// per-lane loop would be serialised lane by lane).
 template <int P, int LS, bool BLOCKED, int WHAT>
 __device__ __forceinline__ void prefetch_tile(const StageArgs& a, long tile) {
   constexpr int NCH = Prec<P>::NCH, NCHL = Prec<P>::NCHL;
@@ -218,14 +212,6 @@ __device__ __forceinline__ void prefetch_tile(const StageArgs& a, long tile) {
       for (int i = warp; i < nrun; i += nw) prefetch_l2_bulk(R + (long)i * a.Vp + base, 512);
     }
   }
-  if constexpr (WHAT >= 3 && !BLOCKED) {
-    const uint4* X = reinterpret_cast<const uint4*>(a.in);
-    for (int d = 0; d < 8; d++) {
-      long j = (long)(__ldg(a.nbr + (long)d * a.Vp + base) & NBR_IDX);
-      if (j > a.Vp_in - 32) j = a.Vp_in - 32;
-      for (int i = warp; i < nrun; i += nw) prefetch_l2_bulk(X + (long)i * a.Vp_in + j, 512);
-    }
-  }
 }
 
 // source array, site stride and presence of the neighbour behind table entry nb
@@ -243,17 +229,6 @@ __device__ __forceinline__ bool nbr_source(const StageArgs& a, uint32_t nb, cons
     }
   }
   return true;
-}
-
-template <int P, bool BLOCKED>
-__device__ __forceinline__ void prefetch_nbr(const StageArgs& a, uint32_t nb, int s) {
-  const void* src;
-  long vs;
-  if (!nbr_source<BLOCKED>(a, nb, src, vs)) return;
-  constexpr int NCH = Prec<P>::NCH;
-  const uint4* p = reinterpret_cast<const uint4*>(src) + ((long)s * NCH) * vs + (nb & NBR_IDX);
-#pragma unroll
-  for (int k = 0; k < NCH; k++) asm volatile("prefetch.global.L1 [%0];" :: "l"(p + k * vs));
 }
 
 // LSM: links from the tile's shared-memory copy lsm ([dir][chunk][32]; lsite = lane)
@@ -578,7 +553,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     if (valid) {
       const long lsite = site;
       constexpr bool LSM = gather_tma(G);
-      HopRing<P, DAG, BLOCKED, G != G_RING_CG, LSM> hp{
+      HopRing<P, DAG, BLOCKED, true, LSM> hp{
           a, site, LSM ? (long)lane : lsite, s, tid, NT, reinterpret_cast<uint4*>(smem_raw), lsm};
       hp.run(acc);
     }
@@ -595,7 +570,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       hop_dir<P, 6, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
       hop_dir<P, 7, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
     }
-  } else if (G == G_BPF || G == G_BPF_LS || G == G_BPF_L) {
+  } else if (G == G_BPF_LS || G == G_BPF_L) {
     prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
     if (valid) {
       const long lsite = site;
@@ -607,29 +582,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       hop_dir<P, 5, DAG, BLOCKED>(acc, a, site, lsite, s);
       hop_dir<P, 6, DAG, BLOCKED>(acc, a, site, lsite, s);
       hop_dir<P, 7, DAG, BLOCKED>(acc, a, site, lsite, s);
-    }
-  } else if (G == G_PF) {
-    if (valid) {
-      const long lsite = site;
-      uint32_t nb[8];
-#pragma unroll
-      for (int d = 0; d < 8; d++) nb[d] = __ldg(a.nbr + (long)d * a.Vp + site);
-      prefetch_nbr<P, BLOCKED>(a, nb[0], s);
-      prefetch_nbr<P, BLOCKED>(a, nb[1], s);
-      hop_dir_nb<P, 0, DAG, BLOCKED>(acc, a, nb[0], lsite, s);
-      prefetch_nbr<P, BLOCKED>(a, nb[2], s);
-      hop_dir_nb<P, 1, DAG, BLOCKED>(acc, a, nb[1], lsite, s);
-      prefetch_nbr<P, BLOCKED>(a, nb[3], s);
-      hop_dir_nb<P, 2, DAG, BLOCKED>(acc, a, nb[2], lsite, s);
-      prefetch_nbr<P, BLOCKED>(a, nb[4], s);
-      hop_dir_nb<P, 3, DAG, BLOCKED>(acc, a, nb[3], lsite, s);
-      prefetch_nbr<P, BLOCKED>(a, nb[5], s);
-      hop_dir_nb<P, 4, DAG, BLOCKED>(acc, a, nb[4], lsite, s);
-      prefetch_nbr<P, BLOCKED>(a, nb[6], s);
-      hop_dir_nb<P, 5, DAG, BLOCKED>(acc, a, nb[5], lsite, s);
-      prefetch_nbr<P, BLOCKED>(a, nb[7], s);
-      hop_dir_nb<P, 6, DAG, BLOCKED>(acc, a, nb[6], lsite, s);
-      hop_dir_nb<P, 7, DAG, BLOCKED>(acc, a, nb[7], lsite, s);
     }
   } else if (valid) {
     const long lsite = site;

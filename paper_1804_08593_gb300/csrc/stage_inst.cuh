@@ -65,19 +65,19 @@ static void stage_cands(StageCand* c, int& n) {
   constexpr bool H16 = (P == P16 || P == PB16);
   if constexpr (POST == 1) {
     // dense CUDA-core post: only where the recurrence is unstable or switched off
-    stage_cand<P, LS, DAG, BLK, POST, 2, H16 ? G_RING_CA : G_REG>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, H16 ? G_RING : G_REG>(c, n, 0);
   } else if constexpr (POST == 2) {
     // tensor-core post: TMEM and the B operands are set up once per CTA, so a persistent
     // grid pays off
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING_CA>(c, n, 2);
-    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING_CA>(c, n, 3);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_RING>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 3, G_RING>(c, n, 3);
   } else if constexpr (H16) {
     // up to Ls = 12 a budget for 3 CTAs per SM (56 registers) wins; beyond, it spills
     constexpr int MB = LS <= 12 ? 3 : 2;
-    stage_cand<P, LS, DAG, BLK, POST, MB, G_RING_CA>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 5 - MB, G_RING_CA>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, MB, G_RING>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 5 - MB, G_RING>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, MB, G_RING_BPF>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, MB, G_RING_TMA>(c, n, 0);
   } else if constexpr (P == P32) {
