@@ -559,8 +559,31 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   DWF_TRY(vop(Em, VOP_ZERO, nullptr, pm));
   if (flex) DWF_TRY(vop(Em, VOP_ZERO, nullptr, rold));
   DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold));
+  // x += alpha p of an outer iteration is deferred into the next update of p (one pass over
+  // x and p instead of two) unless a reliable update needs x first
+  bool x_pending = false;
+  auto flush_x = [&]() -> dwf_status {
+    if (!x_pending) return DWF_OK;
+    x_pending = false;
+    VecArgs va{};
+    va.x = xm;
+    va.p = pm;
+    va.Vp = g.Vp;
+    va.Vhb = g.Vhb;
+    va.Vhb_pad = g.Vhb_pad;
+    va.alpha = dsc + S_ALPHA;
+    va.seg_cps = Em.seg_cps;
+    va.do_x = 1;
+    return vec(Em, va);
+  };
   auto update_p = [&]() -> dwf_status {
     VecArgs va{};
+    if (x_pending) {   // x += alpha p with the old p, then p = z + beta p
+      va.x = xm;
+      va.alpha = dsc + S_ALPHA;
+      va.do_x = 1;
+      x_pending = false;
+    }
     va.p = pm;
     va.r = zm;
     va.u = um;
@@ -590,18 +613,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
     if (flex) DWF_TRY(vop(Em, VOP_COPY, rm, rold));
     DWF_TRY(Em.mpcdag(ym, sm, nullptr, EPI_CG_R, rm, dsc + S_ALPHA,
                       Em.red(FIN_STORE, dsc + S_RR), nullptr));
-    {
-      VecArgs va{};
-      va.x = xm;
-      va.p = pm;
-      va.Vp = g.Vp;
-      va.Vhb = g.Vhb;
-      va.Vhb_pad = g.Vhb_pad;
-      va.alpha = dsc + S_ALPHA;
-      va.seg_cps = Em.seg_cps;
-      va.do_x = 1;
-      DWF_TRY(vec(Em, va));
-    }
+    x_pending = true;
     k++;
     DWF_TRY(read_doubles(h, dsc + S_RR, 1, &rrm));
     hist.push_back(std::sqrt(rrm / bb));
@@ -610,6 +622,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
       break;
     }
     if (rrm <= tol2 || rrm <= delta * delta * anchor) {
+      DWF_TRY(flush_x());
       DWF_TRY(vop(E64, VOP_ADD_CAST, xm, x64, RedArgs{}, 1.0, nullptr, middle));
       DWF_TRY(true_residual(E64, b64, x64, r64, t1, t2, t3, dsc, &rr64));
       if (stats) stats->reliable_updates++;
@@ -627,6 +640,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   }
   if (status == DWF_ERR_NOT_CONVERGED) {
     // fold the current middle iterate into the FP64 solution
+    DWF_TRY(flush_x());
     DWF_TRY(vop(E64, VOP_ADD_CAST, xm, x64, RedArgs{}, 1.0, nullptr, middle));
     DWF_TRY(true_residual(E64, b64, x64, r64, t1, t2, t3, dsc, &rr64));
   }

@@ -23,6 +23,7 @@ CASES = [
     ((4, 4, 2, 2), 10, 1.6, 0.2, 2.0, 1.0, 0.5),     # Ls = 10, b - c != 1... general b, c
     ((4, 4, 2, 4), 8, 1.8, 0.1, 1.25, 0.0, 0.3),     # c = 0, b != 1: D+ = b absorbed
     ((4, 2, 4, 4), 6, 1.8, 0.1, 0.5, 1.5, 0.3),      # |beta/alpha| > 1: matrices only
+    ((4, 2, 2, 4), 4, 1.8, 1.0, 1.5, 0.5, 0.3),      # mf = 1: the walls close without sign change
 ]
 
 

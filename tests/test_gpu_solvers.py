@@ -221,3 +221,19 @@ def test_mspcg_exact_blocks_mixed_precision(inner):
     assert st["true_residual"] <= 1e-10
     assert o.true_residual(U, host(x), phi, p) <= 1.5e-10
     assert rel(host(x), xo) <= 1e-7
+
+
+@pytest.mark.parametrize("solver", ["cg_f64", "cg_f32", "mspcg"])
+def test_zero_source_gives_zero_solution(solver):
+    """phi = 0: every solver returns x = 0 at once (no division by a zero norm)."""
+    dwf = lib()
+    p, U, phi, _, _, _ = c1()
+    h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
+    z = cuda(np.zeros_like(phi))
+    x = cuda(np.ones_like(phi))
+    if solver == "mspcg":
+        st = dwf.dwf_mspcg(h, (2, 2, 2, 2), 2, "f16", "f32", z, x, 1e-10, 100)
+    else:
+        st = dwf.dwf_cg(h, z, x, 1e-10, 100, solver[3:])
+    assert st["iterations"] == 0
+    assert np.count_nonzero(host(x)) == 0
