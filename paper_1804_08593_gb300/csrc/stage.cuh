@@ -11,10 +11,13 @@
 //   D      = M5op - 1/2 Dh D+,   D^dag = M5op^dag - 1/2 D+^dag Dh^dag
 // is one such stage (Sec. 2.2 of the paper: DWF = Wilson hopping x fifth dimension).
 //
-// CTA = 32 consecutive sites x all Ls slices (thread (lane, s)).  Links are read once per site
-// by the first warp and served from L1 to the other Ls-1 warps; the Ls x Ls post matrix is a
-// shared-memory column GEMM over the CTA's 32 sites x 24 reals.  The epilogue optionally
-// fuses the CG residual update r -= alpha * out and a deterministic ||.||^2 reduction.
+// CTA = 32 consecutive sites x all Ls slices (thread (lane, s)).  The tile's links come from
+// DRAM once and are reused by all Ls warps: copied into shared memory by TMA bulk copies, or
+// prefetched into L2 and served from L1.  The Ls x Ls post (D+ M5op^-1 and its adjoint) runs
+// over the CTA's 32 sites x 24 reals in shared memory: by bidiagonal recurrences, as a dense
+// column GEMM, or on the tensor cores.  The epilogue optionally fuses the CG residual update
+// r -= alpha * out and a deterministic ||.||^2 reduction.  Which variant runs is decided per
+// stage kind by the launch autotuner (stage_inst.cuh).
 #pragma once
 
 #include "dwf_device.cuh"
@@ -570,8 +573,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       hop_dir<P, 6, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
       hop_dir<P, 7, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
     }
-  } else if (G == G_BPF_LS || G == G_BPF_L) {
-    prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
+  } else {
+    if constexpr (bpf_what(G) > 0) prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
     if (valid) {
       const long lsite = site;
       hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
@@ -583,16 +586,6 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
       hop_dir<P, 6, DAG, BLOCKED>(acc, a, site, lsite, s);
       hop_dir<P, 7, DAG, BLOCKED>(acc, a, site, lsite, s);
     }
-  } else if (valid) {
-    const long lsite = site;
-    hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
-    hop_dir<P, 1, DAG, BLOCKED>(acc, a, site, lsite, s);
-    hop_dir<P, 2, DAG, BLOCKED>(acc, a, site, lsite, s);
-    hop_dir<P, 3, DAG, BLOCKED>(acc, a, site, lsite, s);
-    hop_dir<P, 4, DAG, BLOCKED>(acc, a, site, lsite, s);
-    hop_dir<P, 5, DAG, BLOCKED>(acc, a, site, lsite, s);
-    hop_dir<P, 6, DAG, BLOCKED>(acc, a, site, lsite, s);
-    hop_dir<P, 7, DAG, BLOCKED>(acc, a, site, lsite, s);
   }
 
   if constexpr (POST == 2 && (P == P16 || P == PB16)) {
