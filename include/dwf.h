@@ -39,8 +39,18 @@
  * describing the last failure.  No C++ exception crosses this interface.  Solver calls
  * write their statistics into *stats when stats is not NULL.
  *
- * Requirements: X, Y, Z, T even and >= 2; 1 <= Ls; Ls in {4, 6, 8, 10, 12, 16} (kernels are
+ * Requirements: X, Y, Z, T even and >= 2; Ls in {4, 6, 8, 10, 12, 16} (kernels are
  * specialised per Ls); the device must be sm_103 (GB300).
+ *
+ * Launch variants: every operator stage exists in a few compiled variants (register budget,
+ * grid shape, how links and neighbours are staged, how the fifth-dimension post matrices are
+ * applied).  Per process, the first launches of each (stage kind, lattice size) that carry no
+ * solver stop flag cycle through them timed with CUDA events, and the fastest is kept.  All
+ * variants agree bit for bit except the tensor-core and recurrence forms of the 16-bit post
+ * (both within the 16-bit tolerance).  Environment switches: DWF_STAGE_VARIANT=<i> forces
+ * variant i; DWF_TUNE_LOG=1 prints each decision on stderr; DWF_POST=matrix|recurrence and
+ * DWF_DISABLE_TC=1 (read by dwf_create) restrict the post forms; DWF_RU_DELTA overrides the
+ * reliable-update threshold 0.1 of the mixed-precision solvers.
  */
 #ifndef DWF_H
 #define DWF_H
