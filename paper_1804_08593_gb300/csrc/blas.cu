@@ -23,6 +23,20 @@ __device__ __forceinline__ bool last_cta(unsigned* counter, unsigned total) {
   return is_last != 0u;
 }
 
+// z = f * src[j] converted to the accumulation type of P (the product in the wider type)
+template <int PZ, int P>
+__device__ __forceinline__ void load_z_as(Spinor<typename Prec<P>::acc>& r, const VecArgs& a,
+                                          long j, int s, double f) {
+  using A = typename Prec<P>::acc;
+  using AZ = typename Prec<PZ>::acc;
+  using AW = typename std::conditional<(PZ == P64 || P == P64), double, float>::type;
+  Spinor<AZ> v;
+  load_spinor<PZ>(v, a.z_src, a.z_vp, j, s);
+  const AW fw = AW(f);
+#pragma unroll
+  for (int k = 0; k < 12; k++) r.c[k] = {A((AW)v.c[k].x * fw), A((AW)v.c[k].y * fw)};
+}
+
 template <int P, int LS>
 __global__ void __launch_bounds__(32 * LS) vec_kernel(const VecArgs a) {
   using A = typename Prec<P>::acc;
@@ -58,7 +72,32 @@ __global__ void __launch_bounds__(32 * LS) vec_kernel(const VecArgs a) {
   if (a.do_p) {
     const A be = A(a.beta[seg]);
     Spinor<A> r;
-    load_spinor<P>(r, a.r, a.Vp, site, s);
+    if (a.z_src) {
+      // the scale once per CTA (FP64 is slow on this part)
+      __shared__ double zf;
+      if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double f = a.z_num;
+        if (a.z_den) {
+          const double d = *a.z_den;
+          f = (d > 0.0 && isfinite(d)) ? sqrt(a.z_num / d) : 1.0;
+        }
+        zf = 1.0 / f;
+      }
+      __syncthreads();
+      const long j = a.z_map ? (long)a.z_map[site] : site;
+      if (j < 0) {
+        zero(r);
+      } else {
+        switch (a.z_prec) {
+          case P64: load_z_as<P64, P>(r, a, j, s, zf); break;
+          case P32: load_z_as<P32, P>(r, a, j, s, zf); break;
+          case P16: load_z_as<P16, P>(r, a, j, s, zf); break;
+          default: load_z_as<PB16, P>(r, a, j, s, zf);
+        }
+      }
+    } else {
+      load_spinor<P>(r, a.r, a.Vp, site, s);
+    }
 #pragma unroll
     for (int k = 0; k < 12; k++) {
       p.c[k].x = r.c[k].x + be * p.c[k].x;
@@ -192,7 +231,7 @@ __global__ void cast_kernel(const CastArgs a) {
   Spinor<AO> w;
 #pragma unroll
   for (int k = 0; k < 12; k++) w.c[k] = {AO((AW)v.c[k].x * f), AO((AW)v.c[k].y * f)};
-  store_spinor<PO>(a.out, a.Vp, site, s, w);
+  if (a.out) store_spinor<PO>(a.out, a.Vp, site, s, w);   // no out: the reduction only
   if (a.out2) store_spinor<PO>(a.out2, a.Vp, site, s, w);
   round_to_storage<PO>(w);   // from here on: the values as stored
   if (a.out3) {

@@ -228,6 +228,16 @@ struct VecArgs {
   void* x;            // x += alpha * p         (if do_x)
   void* p;            // p = r + beta * p       (if do_p)
   const void* r;
+  // z_src (nullable): read r as z = f * z_src[z_map[site]] instead, z_src a field of
+  // precision z_prec and site stride z_vp in another site order (z_map nullable: same order),
+  // f = 1 / sqrt(z_num / *z_den) (1 / z_num without z_den): the preconditioner's output is
+  // used without being stored in this precision first
+  const void* z_src;
+  int z_prec;
+  const int* z_map;
+  long z_vp;
+  double z_num;
+  const double* z_den;
   void* u;            // u = (db + dc K) p_new  (if do_u)
   long Vp;
   int Vhb, Vhb_pad;

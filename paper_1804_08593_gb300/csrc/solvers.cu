@@ -87,7 +87,8 @@ static dwf_status cast(const OpEngine& Eout, int pin, const void* in, void* out,
   a.red = red;
   ProfScope ps(&Eout.h->prof, Eout.h->stream, "cast",
                field_bytes(Eout.g(), pin) +
-                   field_bytes(Eout.g(), Eout.prec) * (1 + (out2 ? 1 : 0) + (out3 ? 1 : 0)) +
+                   field_bytes(Eout.g(), Eout.prec) *
+                       ((out ? 1 : 0) + (out2 ? 1 : 0) + (out3 ? 1 : 0)) +
                    (dotv ? field_bytes(Eout.g(), Eout.prec) : 0),
                0.0);
   DWF_CUDA(launch_cast(pin, Eout.prec, a, Eout.h->Ls, Eout.h->stream));
@@ -95,9 +96,11 @@ static dwf_status cast(const OpEngine& Eout, int pin, const void* in, void* out,
 }
 
 // x/p/u update: bytes = reads of p (+x, r) and writes of x (+p, u).
-static dwf_status vec(const OpEngine& E, const VecArgs& va) {
+static dwf_status vec(const OpEngine& E, const VecArgs& va, double zbytes = 0.0) {
   const double f = (double)field_bytes(E.g(), E.prec);
-  const double bytes = f * (1 + 2 * va.do_x + 2 * va.do_p + va.do_u);
+  // p read; x read and written; r (or the preconditioner output) read and p written; u written
+  const double rb = va.z_src ? zbytes : f;
+  const double bytes = f * (1 + 2 * va.do_x + va.do_p + va.do_u) + (va.do_p ? rb : 0.0);
   char name[32];
   snprintf(name, sizeof(name), "cg_update_%s", prec_name(E.prec));
   ProfScope ps(&E.h->prof, E.h->stream, name, bytes, 0.0);
@@ -392,6 +395,18 @@ __global__ void pr_beta_kernel(double* d) {
   d[S_RHO] = rz;
 }
 
+// Where the outer update reads z from when z is not stored: the local solution in its own
+// site order and precision, with the scale that undoes the local solver's normalisation.
+struct ZSrc {
+  const void* src = nullptr;
+  int prec = 0;
+  const int* map = nullptr;
+  long vp = 0;
+  double num = 1.0;
+  const double* den = nullptr;
+  double bytes = 0.0;
+};
+
 struct InnerVectors {
   void *ri, *xi, *pi, *ui, *ti, *yi, *si;
   bool exact = false;
@@ -401,9 +416,11 @@ struct InnerVectors {
 // z = M^-1 r approximated by l local CG iterations per block from a zero guess (Eqs. 4-5),
 // with every block-local dot product reduced per block; then <r, z> (FR) or the
 // Polak-Ribiere numerator is reduced and beta is finalised on the device.
+// Non-flexible: z is not stored; zs tells the outer update where to read it, and <r, z> (for
+// the Fletcher-Reeves beta) is reduced from the local solution directly.
 static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const void* r, void* z,
                                const InnerVectors& iv, double* dsc, double* blk, int nb, int l,
-                               bool flexible, const void* rold) {
+                               bool flexible, const void* rold, ZSrc& zs) {
   const bool scaled = (Ei.prec == P16 || Ei.prec == PB16);
   const double nreal = 24.0 * Em.h->Ls * (double)(Em.g().V / 2);
   double* rho_b = blk;
@@ -462,9 +479,18 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
     RedArgs rz = Em.red(FIN_BETA, nullptr);
     rz.rho = dsc + S_RHO;
     rz.beta = dsc + S_BETA;
-    DWF_TRY(cast(Em, Ei.prec, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
-                 r, rz, nullptr, remap ? Ei.lay->cb_inv : nullptr, Ei.g().Vp));
+    DWF_TRY(cast(Em, Ei.prec, iv.xi, nullptr, scaled ? nreal : 1.0,
+                 scaled ? dsc + S_RR : nullptr, 1, r, rz, nullptr,
+                 remap ? Ei.lay->cb_inv : nullptr, Ei.g().Vp));
+    zs.src = iv.xi;
+    zs.prec = Ei.prec;
+    zs.map = remap ? Ei.lay->cb_inv : nullptr;
+    zs.vp = Ei.g().Vp;
+    zs.num = scaled ? nreal : 1.0;
+    zs.den = scaled ? dsc + S_RR : nullptr;
+    zs.bytes = (double)field_bytes(Ei.g(), Ei.prec);
   } else {
+    zs = ZSrc{};
     DWF_TRY(cast(Em, Ei.prec, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
                  r, Em.red(FIN_STORE, dsc + S_RZNEW), nullptr,
                  remap ? Ei.lay->cb_inv : nullptr, Ei.g().Vp));
@@ -558,7 +584,8 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   DWF_TRY(vop(Em, VOP_ZERO, nullptr, xm));
   DWF_TRY(vop(Em, VOP_ZERO, nullptr, pm));
   if (flex) DWF_TRY(vop(Em, VOP_ZERO, nullptr, rold));
-  DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold));
+  ZSrc zs;
+  DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold, zs));
   // x += alpha p of an outer iteration is deferred into the next update of p (one pass over
   // x and p instead of two) unless a reliable update needs x first
   bool x_pending = false;
@@ -586,6 +613,12 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
     }
     va.p = pm;
     va.r = zm;
+    va.z_src = zs.src;
+    va.z_prec = zs.prec;
+    va.z_map = zs.map;
+    va.z_vp = zs.vp;
+    va.z_num = zs.num;
+    va.z_den = zs.den;
     va.u = um;
     va.Vp = g.Vp;
     va.Vhb = g.Vhb;
@@ -597,7 +630,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
     va.db = h->b;
     va.dc = h->c;
     va.mf = h->mf;
-    return vec(Em, va);
+    return vec(Em, va, zs.bytes);
   };
   DWF_TRY(update_p());
   double anchor = rr64;
@@ -634,7 +667,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
       DWF_TRY(vop(Em, VOP_ZERO, nullptr, xm));
       anchor = rr64;
     }
-    DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold));
+    DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold, zs));
     inner_total += l;
     DWF_TRY(update_p());
   }
