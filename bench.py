@@ -53,6 +53,8 @@ def args_parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched workload (64 uneven Moebius solves in one call)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the MSPCG runs with more local iterations (l = 2, 6)")
     ap.add_argument("--case", default="solve", choices=["solve", "apply"],
                     help="apply: only K applications of Mpc^dag Mpc (for profiler captures)")
     ap.add_argument("--prec", default="f16", help="precision of --case apply")
@@ -328,6 +330,21 @@ def run_ours(a):
                               "reliable_updates": st["reliable_updates"],
                               "true_residual": st["true_residual"]}
 
+    # the same solve with more local iterations: the paper's trade of global iterations (g)
+    # for local work, for comparison with the default
+    sweep = {}
+    if not a.no_sweep:
+        for lv in (2, 6):
+            xs = torch.zeros_like(phi_d)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = dwf.dwf_mspcg(h, cfg["block"], lv, a.inner, "f32", phi_d, xs, TOL, 20000,
+                               local_op=lop)
+            torch.cuda.synchronize()
+            sweep[f"l={lv}"] = {"seconds": time.perf_counter() - t0,
+                                "outer_iterations": st["iterations"],
+                                "true_residual": st["true_residual"]}
+
     # batched workload: 64 independent Moebius solves of uneven sizes in one call
     batch = None
     if not a.no_batch:
@@ -395,6 +412,8 @@ def run_ours(a):
         line["plain_cg"] = plain_cg
     if batch:
         line["batch"] = batch
+    if sweep:
+        line["mspcg_more_local_iterations"] = sweep
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
