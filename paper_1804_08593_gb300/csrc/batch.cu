@@ -14,6 +14,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "engine.h"
@@ -548,15 +550,19 @@ dwf_status build_group(Batch& B, Group& G, const dwf_problem* pr) {
 // Autotuner: times stage A of the group for candidate persistent grid sizes (CTAs per SM) and
 // keeps the fastest; results are cached per (Ls, tile count) for the process.
 dwf_status autotune(Group& G, cudaStream_t st) {
-  static std::map<std::pair<int, long>, int> cache;
-  auto key = std::make_pair(G.Ls, G.ntiles);
-  auto it = cache.find(key);
-  if (it != cache.end()) {
-    G.grid = it->second;
-    return DWF_OK;
-  }
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, long>, int> cache;   // (device, Ls, tiles) -> grid
   int dev, sms;
   DWF_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, G.Ls, G.ntiles);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      G.grid = it->second;
+      return DWF_OK;
+    }
+  }
   DWF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int cand[] = {1, 2, 3, 4, 0};
   cudaEvent_t e0, e1;
@@ -590,7 +596,10 @@ dwf_status autotune(Group& G, cudaStream_t st) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   G.grid = best_grid;
-  cache[key] = best_grid;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best_grid;
+  }
   return DWF_OK;
 }
 

@@ -2,11 +2,24 @@
 // u = D+ p), precision casts with a scale and a fused dot product, and small vector ops.
 // All use CTA = 32 sites x Ls slices so that reductions are segmented per lattice block
 // exactly like the operator stages (segment = CTA index / (Vhb_pad / 32)).
+#include <atomic>
 #include <type_traits>
 
 #include "dwf_internal.h"
 
 namespace dwf {
+
+// Sets a kernel's dynamic shared memory limit once per device (one bit per device ordinal).
+template <typename K>
+static cudaError_t set_smem_once(K kernel, std::atomic<uint64_t>& done, int bytes) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+  if (done.load() & bit) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
 
 // Completion counting without data: returns true in every thread of the last CTA to finish
 // (of `total` CTAs that count on this counter).
@@ -152,14 +165,9 @@ template <int P, int LS>
 static cudaError_t vec_launch(const VecArgs& a, cudaStream_t st) {
   using A = typename Prec<P>::acc;
   const size_t sm = a.do_u ? (size_t)LS * 24 * 32 * sizeof(A) : 0;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(vec_kernel<P, LS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(LS * 24 * 32 * sizeof(A)));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  cudaError_t e = set_smem_once(vec_kernel<P, LS>, attr, (int)(LS * 24 * 32 * sizeof(A)));
+  if (e != cudaSuccess) return e;
   vec_kernel<P, LS><<<dim3((unsigned)(a.Vp / 32)), dim3(32, LS), sm, st>>>(a);
   return cudaGetLastError();
 }
@@ -287,14 +295,9 @@ __global__ void cast_kernel(const CastArgs a) {
 template <int PI, int PO>
 static cudaError_t cast_go(const CastArgs& a, dim3 g, dim3 b, cudaStream_t st) {
   using AO = typename Prec<PO>::acc;
-  static bool attr = false;
-  if (!attr) {   // room for the D+ exchange of the largest Ls
-    cudaError_t e = cudaFuncSetAttribute(cast_kernel<PI, PO>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(16 * 24 * 32 * sizeof(AO)));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};   // room for the D+ exchange of the largest Ls
+  cudaError_t e = set_smem_once(cast_kernel<PI, PO>, attr, (int)(16 * 24 * 32 * sizeof(AO)));
+  if (e != cudaSuccess) return e;
   const size_t sm = a.out3 ? (size_t)b.y * 24 * 32 * sizeof(AO) : 0;
   cast_kernel<PI, PO><<<g, b, sm, st>>>(a);
   return cudaGetLastError();

@@ -3,22 +3,34 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <map>
+#include <mutex>
+#include <tuple>
 
 #include "dwf_internal.h"
 
 namespace dwf {
 
+// the current device's ordinal (host state below is kept per device)
+static int current_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev;
+}
+
 template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G>
 static cudaError_t stage_launch_v(const StageArgs& b, size_t sm, long g, cudaStream_t st) {
   auto k = stage_kernel<P, LS, DAG, BLK, POST, MINB, G>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<uint64_t> attr_set{0};   // one bit per device
+  const int dev = current_device();
+  const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
+  if (!(attr_set.load() & bit)) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.fetch_or(bit);
   }
   k<<<dim3((unsigned)g), dim3(32, LS), sm, st>>>(b);
   return cudaGetLastError();
@@ -93,13 +105,10 @@ static void stage_cands(StageCand* c, int& n) {
 }
 
 static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 1;
-  }
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, current_device()) !=
+          cudaSuccess || n <= 0)
+    n = 1;
   return n;
 }
 
@@ -137,8 +146,11 @@ static cudaError_t stage_launch_one(const StageArgs& a, cudaStream_t st) {
     if (b.grid > 0) return std::min<long>(b.grid, b.ntiles);
     return k.per_sm ? std::min<long>((long)k.per_sm * sm_count(), b.ntiles) : b.ntiles;
   };
-  static std::map<std::pair<long, int>, StageTune> tunes;   // per (tile count, kind)
-  StageTune& T = tunes[{b.ntiles, kind}];
+  // per (device, tile count, kind); handles on different host threads share it
+  static std::mutex mu;
+  static std::map<std::tuple<int, long, int>, StageTune> tunes;
+  std::lock_guard<std::mutex> lock(mu);
+  StageTune& T = tunes[std::make_tuple(current_device(), b.ntiles, kind)];
   const int nt = TUNE_ROUNDS * n;                           // timed launches
   const int nl = nt + n;                                    // tuning launches
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
