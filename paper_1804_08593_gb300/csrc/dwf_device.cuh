@@ -229,11 +229,12 @@ template <typename A> __device__ __forceinline__ void zero(Spinor<A>& s) {
 // spins are sgn * B^dag times the projected upper half-spinor h = psi_up + sgn*B psi_dn.
 // B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.
 // ---------------------------------------------------------------------------------------
-template <int P, int MU, bool SMEM = false>
-__device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
-                                         const Spinor<typename Prec<P>::acc>& psi,
-                                         const void* links, long Vp, long site, int dir,
-                                         typename Prec<P>::acc sgn) {
+// the same term with the link matrix u already in registers
+template <int P, int MU>
+__device__ __forceinline__ void hop_term_u(Spinor<typename Prec<P>::acc>& acc,
+                                           const Spinor<typename Prec<P>::acc>& psi,
+                                           const cx<typename Prec<P>::acc> (&u)[9],
+                                           typename Prec<P>::acc sgn) {
   using A = typename Prec<P>::acc;
   cx<A> h[2][3];
 #pragma unroll
@@ -256,8 +257,6 @@ __device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
     h[0][a] = {p0.x + sgn * b0.x, p0.y + sgn * b0.y};
     h[1][a] = {p1.x + sgn * b1.x, p1.y + sgn * b1.y};
   }
-  cx<A> u[9];
-  load_link9<P, SMEM>(u, links, Vp, site, dir);
   cx<A> g[2][3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
@@ -290,6 +289,16 @@ __device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
     acc.c[6 + a] = {acc.c[6 + a].x + sgn * l0.x, acc.c[6 + a].y + sgn * l0.y};
     acc.c[9 + a] = {acc.c[9 + a].x + sgn * l1.x, acc.c[9 + a].y + sgn * l1.y};
   }
+}
+
+template <int P, int MU, bool SMEM = false>
+__device__ __forceinline__ void hop_term(Spinor<typename Prec<P>::acc>& acc,
+                                         const Spinor<typename Prec<P>::acc>& psi,
+                                         const void* links, long Vp, long site, int dir,
+                                         typename Prec<P>::acc sgn) {
+  cx<typename Prec<P>::acc> u[9];
+  load_link9<P, SMEM>(u, links, Vp, site, dir);
+  hop_term_u<P, MU>(acc, psi, u, sgn);
 }
 
 // Neighbour table entries: index of the neighbour in the other parity's site order; bit 31

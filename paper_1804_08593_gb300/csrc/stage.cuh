@@ -497,16 +497,56 @@ __host__ __device__ constexpr size_t tma_link_offset(int Ls, int post, int gathe
 // POST: 0 = no post matrix, 1 = CUDA-core column GEMM, 2 = tensor cores (16-bit only),
 //       3 = D+^dag applied sparsely (b + c K^dag: neighbours in s through shared memory),
 //       4 = D+ M5op^-1 (dag: M5op^-dag D+^dag) by an O(Ls) recurrence per column
-template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G>
+// One direction of the paired-slice hop: neighbour spinors of slices w and w + lsp, the link
+// (from the tile's shared-memory copy) loaded once for both.
+template <int P, int D, bool DAG, bool BLOCKED>
+__device__ __forceinline__ void hop_pair_d(Spinor<typename Prec<P>::acc> (&acc)[2],
+                                           const StageArgs& a, long site, int lane, int w,
+                                           int lsp, const uint4* lsm) {
+  using A = typename Prec<P>::acc;
+  const uint32_t nb = __ldg(a.nbr + (long)D * a.Vp + site);
+  const void* src;
+  long vs;
+  if (!nbr_source<BLOCKED>(a, nb, src, vs)) return;
+  const long j = (long)(nb & NBR_IDX);
+  constexpr bool back = (D & 1) != 0;
+  const A sgn = (back != DAG) ? A(1) : A(-1);
+  Spinor<A> psi0, psi1;
+  load_spinor<P>(psi0, src, vs, j, w);
+  load_spinor<P>(psi1, src, vs, j, w + lsp);
+  cx<A> u[9];
+  load_link9<P, true>(u, lsm, 32, lane, D);
+  hop_term_u<P, D / 2>(acc[0], psi0, u, sgn);
+  hop_term_u<P, D / 2>(acc[1], psi1, u, sgn);
+}
+
+template <int P, bool DAG, bool BLOCKED>
+__device__ __forceinline__ void hop_pair(Spinor<typename Prec<P>::acc> (&acc)[2],
+                                         const StageArgs& a, long site, int lane, int w,
+                                         int lsp, const uint4* lsm) {
+  hop_pair_d<P, 0, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 1, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 2, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 3, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 4, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 5, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 6, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 7, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+}
+
+// SP: slices per thread (1, or 2 for the FP32 paired-slice variant: thread (lane, w) computes
+// slices w and w + Ls/2 and loads each link once for both).
+template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G, int SP = 1>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
                                            unsigned char* smem_raw, double* red_scratch,
                                            uint64_t* tc_mbar, uint32_t* tc_slot,
                                            uint32_t& tc_phase, uint64_t* lk_mbar,
                                            uint32_t& lk_phase) {
   using A = typename Prec<P>::acc;
-  const int lane = threadIdx.x, s = threadIdx.y;
-  const int tid = lane + 32 * s;
-  constexpr int NT = 32 * LS;
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int tid = lane + 32 * w;
+  constexpr int NT = 32 * LS / SP;
+  constexpr int LSP = LS / SP;   // distance between a thread's slices
   const long site = tile * 32 + lane;
   int seg, ntl, jl, vh;
   long first;
@@ -533,8 +573,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   // this tile's fifth-dimension coefficients (per problem when batched), read where used
   auto K5 = [&]() -> Coef5<A> { return a.tile_seg ? coef5<A>(a.segp[seg]) : coef5<A>(a); };
 
-  Spinor<A> acc;
-  zero(acc);
+  Spinor<A> acc[SP];
+#pragma unroll
+  for (int j = 0; j < SP; j++) zero(acc[j]);
   // G_TMA / G_RING_TMA: stage the tile's links in shared memory (after the ring / post area)
   const uint4* lsm = nullptr;
   if constexpr (gather_tma(G)) {
@@ -551,65 +592,80 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     lk_phase ^= 1u;
     lsm = reinterpret_cast<const uint4*>(lk);
   }
-  if constexpr (gather_ring(G)) {
-    if constexpr (G == G_RING_BPF) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
-    if (valid) {
-      const long lsite = site;
-      constexpr bool LSM = gather_tma(G);
-      HopRing<P, DAG, BLOCKED, true, LSM> hp{
-          a, site, LSM ? (long)lane : lsite, s, tid, NT, reinterpret_cast<uint4*>(smem_raw), lsm};
-      hp.run(acc);
-    }
-    // the post stage reuses shared memory that other threads' rings occupy
-    __syncthreads();
-  } else if (G == G_TMA) {
-    if (valid) {
-      hop_dir<P, 0, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
-      hop_dir<P, 1, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
-      hop_dir<P, 2, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
-      hop_dir<P, 3, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
-      hop_dir<P, 4, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
-      hop_dir<P, 5, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
-      hop_dir<P, 6, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
-      hop_dir<P, 7, DAG, BLOCKED, true>(acc, a, site, lane, s, lsm);
+  if constexpr (SP == 1) {
+    const int s = w;
+    if constexpr (gather_ring(G)) {
+      if constexpr (G == G_RING_BPF) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
+      if (valid) {
+        const long lsite = site;
+        constexpr bool LSM = gather_tma(G);
+        HopRing<P, DAG, BLOCKED, true, LSM> hp{
+            a, site, LSM ? (long)lane : lsite, s, tid, NT, reinterpret_cast<uint4*>(smem_raw), lsm};
+        hp.run(acc[0]);
+      }
+      // the post stage reuses shared memory that other threads' rings occupy
+      __syncthreads();
+    } else if (G == G_TMA) {
+      if (valid) {
+        hop_dir<P, 0, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 1, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 2, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 3, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 4, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 5, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 6, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 7, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+      }
+    } else {
+      if constexpr (bpf_what(G) > 0) prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
+      if (valid) {
+        const long lsite = site;
+        hop_dir<P, 0, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 1, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 2, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 3, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 4, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 5, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 6, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 7, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+      }
     }
   } else {
-    if constexpr (bpf_what(G) > 0) prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
+    // paired slices (FP32, links staged in shared memory): one link load serves both slices
+    static_assert(SP == 1 || gather_tma(G), "paired slices read the links from shared memory");
     if (valid) {
-      const long lsite = site;
-      hop_dir<P, 0, DAG, BLOCKED>(acc, a, site, lsite, s);
-      hop_dir<P, 1, DAG, BLOCKED>(acc, a, site, lsite, s);
-      hop_dir<P, 2, DAG, BLOCKED>(acc, a, site, lsite, s);
-      hop_dir<P, 3, DAG, BLOCKED>(acc, a, site, lsite, s);
-      hop_dir<P, 4, DAG, BLOCKED>(acc, a, site, lsite, s);
-      hop_dir<P, 5, DAG, BLOCKED>(acc, a, site, lsite, s);
-      hop_dir<P, 6, DAG, BLOCKED>(acc, a, site, lsite, s);
-      hop_dir<P, 7, DAG, BLOCKED>(acc, a, site, lsite, s);
+      if constexpr (SP == 2) hop_pair<P, DAG, BLOCKED>(acc, a, site, lane, w, LSP, lsm);
     }
   }
 
-  if constexpr (POST == 2 && (P == P16 || P == PB16)) {
-    post_tensor_core<LS>(acc, a, lane, s, tid, smem_raw, tc_mbar, tc_slot, tc_phase);
+  if constexpr (POST == 2 && (P == P16 || P == PB16) && SP == 1) {
+    post_tensor_core<LS>(acc[0], a, lane, w, tid, smem_raw, tc_mbar, tc_slot, tc_phase);
   }
   if constexpr (POST == 3) {
     // D+^dag h at s = b h_s + c (P+ h_{s+1} + P- h_{s-1}),  h_{Ls} = -mf h_0, h_{-1} = -mf h_{Ls-1}
     A* buf = reinterpret_cast<A*>(smem_raw);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      buf[(s * 24 + 2 * k) * 32 + lane] = acc.c[k].x;
-      buf[(s * 24 + 2 * k + 1) * 32 + lane] = acc.c[k].y;
-    }
+    for (int j = 0; j < SP; j++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane] = acc[j].c[k].x;
+        buf[((w + j * LSP) * 24 + 2 * k + 1) * 32 + lane] = acc[j].c[k].y;
+      }
     __syncthreads();
     const Coef5<A> C = K5();
-    const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
-    const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
     const A b_ = C.db, c_ = C.dc;
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      const int sn = k < 6 ? su : sd;
-      const A f = k < 6 ? fu : fd;
-      acc.c[k].x = b_ * acc.c[k].x + c_ * f * buf[(sn * 24 + 2 * k) * 32 + lane];
-      acc.c[k].y = b_ * acc.c[k].y + c_ * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+    for (int j = 0; j < SP; j++) {
+      const int s = w + j * LSP;
+      const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
+      const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        const int sn = k < 6 ? su : sd;
+        const A f = k < 6 ? fu : fd;
+        acc[j].c[k].x = b_ * acc[j].c[k].x + c_ * f * buf[(sn * 24 + 2 * k) * 32 + lane];
+        acc[j].c[k].y = b_ * acc[j].c[k].y + c_ * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+      }
     }
   }
   if constexpr (POST == 4) {
@@ -621,10 +677,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     //   upper: mirror image, kappa = r mf / (1 + mf (-r)^Ls);  M5op^-1 v = z / alpha.
     A* buf = reinterpret_cast<A*>(smem_raw);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      buf[(s * 24 + 2 * k) * 32 + lane] = acc.c[k].x;
-      buf[(s * 24 + 2 * k + 1) * 32 + lane] = acc.c[k].y;
-    }
+    for (int j = 0; j < SP; j++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane] = acc[j].c[k].x;
+        buf[((w + j * LSP) * 24 + 2 * k + 1) * 32 + lane] = acc[j].c[k].y;
+      }
     __syncthreads();
     const Coef5<A> C = K5();
     const A r = C.r, inva = C.inva, kappa = C.kappa;
@@ -683,10 +741,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      acc.c[k].x = buf[(s * 24 + 2 * k) * 32 + lane];
-      acc.c[k].y = buf[(s * 24 + 2 * k + 1) * 32 + lane];
-    }
+    for (int j = 0; j < SP; j++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        acc[j].c[k].x = buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane];
+        acc[j].c[k].y = buf[((w + j * LSP) * 24 + 2 * k + 1) * 32 + lane];
+      }
   }
   if constexpr (POST == 1) {
     // Dense per-chirality Ls x Ls matrix along s: buf[s][24][32] holds the CTA's hop results;
@@ -696,10 +756,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     const A* pm = reinterpret_cast<const A*>(post);
     for (int i = tid; i < 2 * LS * LS; i += NT) mat[i] = pm[i];
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      buf[(s * 24 + 2 * k) * 32 + lane] = acc.c[k].x;
-      buf[(s * 24 + 2 * k + 1) * 32 + lane] = acc.c[k].y;
-    }
+    for (int j = 0; j < SP; j++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane] = acc[j].c[k].x;
+        buf[((w + j * LSP) * 24 + 2 * k + 1) * 32 + lane] = acc[j].c[k].y;
+      }
     __syncthreads();
     for (int col = tid; col < 24 * 32; col += NT) {
       const int c = col >> 5, l = col & 31;
@@ -717,65 +779,72 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      acc.c[k].x = buf[(s * 24 + 2 * k) * 32 + lane];
-      acc.c[k].y = buf[(s * 24 + 2 * k + 1) * 32 + lane];
-    }
-  }
-
-  A hs;
-  if constexpr (sizeof(A) == 8) hs = a.hop_scale; else hs = a.hs32;
+    for (int j = 0; j < SP; j++)
 #pragma unroll
-  for (int k = 0; k < 12; k++) acc.c[k] = cscale(hs, acc.c[k]);
-
-  if (a.local_mode != LOC_NONE && valid) {
-    // M5op x at s = alpha x_s + beta (P- x_{s+1} + P+ x_{s-1});
-    // M5op^dag x at s = alpha x_s + beta (P+ x_{s+1} + P- x_{s-1});
-    // x_{Ls} = -mf x_0, x_{-1} = -mf x_{Ls-1}.
-    Spinor<A> x0, xu, xd;
-    load_spinor<P>(x0, a.in2, a.Vp, site, s);
-    load_spinor<P>(xu, a.in2, a.Vp, site, s + 1 < LS ? s + 1 : 0);
-    load_spinor<P>(xd, a.in2, a.Vp, site, s > 0 ? s - 1 : LS - 1);
-    const Coef5<A> C = K5();
-    const A fu = (s + 1 < LS) ? A(1) : -C.mf;
-    const A fd = (s > 0) ? A(1) : -C.mf;
-    const A la = C.la, lb = C.lb;
-    const bool dagm = (a.local_mode == LOC_M5DAG);
-#pragma unroll
-    for (int k = 0; k < 12; k++) {
-      const bool plus = k < 6;
-      const bool from_up = dagm ? plus : !plus;
-      const cx<A> nb = from_up ? cscale(fu, xu.c[k]) : cscale(fd, xd.c[k]);
-      acc.c[k].x += la * x0.c[k].x + lb * nb.x;
-      acc.c[k].y += la * x0.c[k].y + lb * nb.y;
-    }
+      for (int k = 0; k < 12; k++) {
+        acc[j].c[k].x = buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane];
+        acc[j].c[k].y = buf[((w + j * LSP) * 24 + 2 * k + 1) * 32 + lane];
+      }
   }
 
   A nrm = A(0);   // this thread's share of the reduction, in the accumulation type
-  if (a.epi == EPI_CG_R) {
-    const A al = A(a.alpha[seg]);
-    Spinor<A> rr;
-    load_spinor<P>(rr, a.r, a.Vp, site, s);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      rr.c[k].x -= al * acc.c[k].x;
-      rr.c[k].y -= al * acc.c[k].y;
+  for (int jj = 0; jj < SP; jj++) {
+    const int s = w + jj * LSP;
+    Spinor<A>& acc_j = acc[jj];
+    A hs;
+    if constexpr (sizeof(A) == 8) hs = a.hop_scale; else hs = a.hs32;
+  #pragma unroll
+    for (int k = 0; k < 12; k++) acc_j.c[k] = cscale(hs, acc_j.c[k]);
+
+    if (a.local_mode != LOC_NONE && valid) {
+      // M5op x at s = alpha x_s + beta (P- x_{s+1} + P+ x_{s-1});
+      // M5op^dag x at s = alpha x_s + beta (P+ x_{s+1} + P- x_{s-1});
+      // x_{Ls} = -mf x_0, x_{-1} = -mf x_{Ls-1}.
+      Spinor<A> x0, xu, xd;
+      load_spinor<P>(x0, a.in2, a.Vp, site, s);
+      load_spinor<P>(xu, a.in2, a.Vp, site, s + 1 < LS ? s + 1 : 0);
+      load_spinor<P>(xd, a.in2, a.Vp, site, s > 0 ? s - 1 : LS - 1);
+      const Coef5<A> C = K5();
+      const A fu = (s + 1 < LS) ? A(1) : -C.mf;
+      const A fd = (s > 0) ? A(1) : -C.mf;
+      const A la = C.la, lb = C.lb;
+      const bool dagm = (a.local_mode == LOC_M5DAG);
+  #pragma unroll
+      for (int k = 0; k < 12; k++) {
+        const bool plus = k < 6;
+        const bool from_up = dagm ? plus : !plus;
+        const cx<A> nb = from_up ? cscale(fu, xu.c[k]) : cscale(fd, xd.c[k]);
+        acc_j.c[k].x += la * x0.c[k].x + lb * nb.x;
+        acc_j.c[k].y += la * x0.c[k].y + lb * nb.y;
+      }
     }
-    store_spinor<P>(a.r, a.Vp, site, s, rr);
-    // the norm of what was stored (rounded to the storage precision)
-    Spinor<A> back = rr;
-    round_to_storage<P>(back);
-    A part = A(0);   // per-thread partial in the accumulation type; FP64 across threads
-#pragma unroll
-    for (int k = 0; k < 12; k++) part = fma(back.c[k].x, back.c[k].x, fma(back.c[k].y, back.c[k].y, part));
-    nrm = part;
-  } else {
-    if (a.epi != EPI_NORM_ONLY) store_spinor<P>(a.out, a.Vp, site, s, acc);
-    if (a.epi == EPI_NORM || a.epi == EPI_NORM_ONLY) {
-      A part = A(0);
-#pragma unroll
-      for (int k = 0; k < 12; k++) part = fma(acc.c[k].x, acc.c[k].x, fma(acc.c[k].y, acc.c[k].y, part));
-      nrm = part;
+
+    if (a.epi == EPI_CG_R) {
+      const A al = A(a.alpha[seg]);
+      Spinor<A> rr;
+      load_spinor<P>(rr, a.r, a.Vp, site, s);
+  #pragma unroll
+      for (int k = 0; k < 12; k++) {
+        rr.c[k].x -= al * acc_j.c[k].x;
+        rr.c[k].y -= al * acc_j.c[k].y;
+      }
+      store_spinor<P>(a.r, a.Vp, site, s, rr);
+      // the norm of what was stored (rounded to the storage precision)
+      Spinor<A> back = rr;
+      round_to_storage<P>(back);
+      A part = A(0);   // per-thread partial in the accumulation type; FP64 across threads
+  #pragma unroll
+      for (int k = 0; k < 12; k++) part = fma(back.c[k].x, back.c[k].x, fma(back.c[k].y, back.c[k].y, part));
+      nrm += part;
+    } else {
+      if (a.epi != EPI_NORM_ONLY) store_spinor<P>(a.out, a.Vp, site, s, acc_j);
+      if (a.epi == EPI_NORM || a.epi == EPI_NORM_ONLY) {
+        A part = A(0);
+  #pragma unroll
+        for (int k = 0; k < 12; k++) part = fma(acc_j.c[k].x, acc_j.c[k].x, fma(acc_j.c[k].y, acc_j.c[k].y, part));
+        nrm += part;
+      }
     }
   }
   if (a.epi != EPI_STORE) {
@@ -786,9 +855,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
 
 // MINB = resident CTAs per SM the register budget is sized for (2 or 3); the launcher's
 // autotuner picks the faster one per kernel configuration.
-// G: how the neighbours are gathered (enum Gather).
-template <int P, int LS, bool DAG, bool BLOCKED, int POST, int MINB, int G>
-__global__ void __launch_bounds__(32 * LS, MINB) stage_kernel(const StageArgs a) {
+// G: how the neighbours are gathered (enum Gather); SP: slices per thread (block 32 x Ls/SP).
+template <int P, int LS, bool DAG, bool BLOCKED, int POST, int MINB, int G, int SP = 1>
+__global__ void __launch_bounds__(32 * LS / SP, MINB) stage_kernel(const StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red_scratch[32];
   __shared__ uint64_t tc_mbar;
@@ -802,8 +871,8 @@ __global__ void __launch_bounds__(32 * LS, MINB) stage_kernel(const StageArgs a)
   }
   uint32_t tc_phase = 0, lk_phase = 0;
   for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    stage_tile<P, LS, DAG, BLOCKED, POST, G>(a, tile, smem_raw, red_scratch, &tc_mbar,
-                                             &tc_slot, tc_phase, &lk_mbar, lk_phase);
+    stage_tile<P, LS, DAG, BLOCKED, POST, G, SP>(a, tile, smem_raw, red_scratch, &tc_mbar,
+                                                 &tc_slot, tc_phase, &lk_mbar, lk_phase);
     __syncthreads();
   }
   if constexpr (TC) tc_teardown(&tc_slot);

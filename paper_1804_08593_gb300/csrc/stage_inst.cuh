@@ -21,9 +21,9 @@ static int current_device() {
   return dev;
 }
 
-template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G>
+template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G, int SP = 1>
 static cudaError_t stage_launch_v(const StageArgs& b, size_t sm, long g, cudaStream_t st) {
-  auto k = stage_kernel<P, LS, DAG, BLK, POST, MINB, G>;
+  auto k = stage_kernel<P, LS, DAG, BLK, POST, MINB, G, SP>;
   static std::atomic<uint64_t> attr_set{0};   // one bit per device
   const int dev = current_device();
   const uint64_t bit = dev < 64 ? (uint64_t)1 << dev : 0;
@@ -32,7 +32,7 @@ static cudaError_t stage_launch_v(const StageArgs& b, size_t sm, long g, cudaStr
     if (e != cudaSuccess) return e;
     attr_set.fetch_or(bit);
   }
-  k<<<dim3((unsigned)g), dim3(32, LS), sm, st>>>(b);
+  k<<<dim3((unsigned)g), dim3(32, LS / SP), sm, st>>>(b);
   return cudaGetLastError();
 }
 
@@ -48,7 +48,7 @@ struct StageCand {
   StageFn fn;
   size_t smem;
   int per_sm;            // 0: one CTA per tile; k: persistent grid of k CTAs per SM
-  int post, minb, gather;  // for the tuning log
+  int post, minb, gather, sp;  // for the tuning log
 };
 constexpr int MAX_CANDS = 12;
 constexpr int TUNE_ROUNDS = 2;   // timed rounds after one untimed round (first-launch costs)
@@ -67,10 +67,10 @@ struct StageTune {
 // measured slower.  FP16/BF16 gather through the L1-cached cp.async ring with a register
 // budget for 2 or 3 CTAs per SM, with the tile's links and streams prefetched into L2 or its
 // links staged in shared memory by TMA.  FP64 (ALU bound): one CTA per tile or persistent.
-template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G>
+template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G, int SP = 1>
 static void stage_cand(StageCand* c, int& n, int per_sm) {
-  c[n++] = {stage_launch_v<P, LS, DAG, BLK, POST, MINB, G>,
-            stage_smem_bytes<P>(LS, POST, G), per_sm, POST, MINB, G};
+  c[n++] = {stage_launch_v<P, LS, DAG, BLK, POST, MINB, G, SP>,
+            stage_smem_bytes<P>(LS, POST, G), per_sm, POST, MINB, G, SP};
 }
 template <int P, int LS, bool DAG, bool BLK, int POST>
 static void stage_cands(StageCand* c, int& n) {
@@ -98,6 +98,9 @@ static void stage_cands(StageCand* c, int& n) {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_BPF_LS>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA>(c, n, 2);
+    // two slices per thread, one link load for both (half the warps, twice the loads each)
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, 2>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, 2>(c, n, 2);
   } else {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);
@@ -180,8 +183,9 @@ static cudaError_t stage_launch_one(const StageArgs& a, cudaStream_t st) {
         fprintf(stderr, "dwf tune P%d Ls%d dag%d blk%d tiles %ld:", P, LS, (int)DAG, (int)BLK,
                 b.ntiles);
         for (int k = 0; k < n; k++)
-          fprintf(stderr, " %s[post%d minb%d gather%d sm%d %.1fus]", k == T.chosen ? "*" : "",
-                  c[k].post, c[k].minb, c[k].gather, c[k].per_sm, 1000.f * tks[k] / TUNE_ROUNDS);
+          fprintf(stderr, " %s[post%d minb%d gather%d sp%d sm%d %.1fus]", k == T.chosen ? "*" : "",
+                  c[k].post, c[k].minb, c[k].gather, c[k].sp, c[k].per_sm,
+                  1000.f * tks[k] / TUNE_ROUNDS);
         fprintf(stderr, "\n");
       }
       for (auto& e : T.ev)

@@ -162,3 +162,21 @@ def test_post_by_matrix_and_by_recurrence(case, prec, mode, monkeypatch):
         out = cuda(np.zeros_like(x))
         dwf.dwf_apply(h, op, cuda(x), out, prec)
         assert rel(host(out), ref) <= TOL[prec], (op, rel(host(out), ref))
+
+
+@pytest.mark.parametrize("variant", [str(i) for i in range(7)])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
+def test_every_launch_variant_matches_oracle(variant, prec, monkeypatch):
+    """Every compiled launch variant of the stages (register budget, grid, link staging,
+    neighbour gather, slices per thread), forced with DWF_STAGE_VARIANT, meets the operator
+    tolerance on a lattice with a ragged tail, in the full and the dagger stages."""
+    dwf = lib()
+    rng, U, p = _setup(CASES[1], 13)
+    x = rand_even(rng, p.dims, p.Ls)
+    monkeypatch.setenv("DWF_STAGE_VARIANT", variant)
+    h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
+    for op, ref in (("Mpc", o.mpc(U, x, p)), ("Mpc_dag", o.mpc_dag(U, x, p)),
+                    ("MdagM", o.mdagm(U, x, p))):
+        out = cuda(np.zeros_like(x))
+        dwf.dwf_apply(h, op, cuda(x), out, prec)
+        assert rel(host(out), ref) <= TOL[prec], (variant, op, rel(host(out), ref))
