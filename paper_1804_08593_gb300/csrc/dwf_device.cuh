@@ -229,14 +229,9 @@ template <typename A> __device__ __forceinline__ void zero(Spinor<A>& s) {
 // spins are sgn * B^dag times the projected upper half-spinor h = psi_up + sgn*B psi_dn.
 // B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.
 // ---------------------------------------------------------------------------------------
-// the same term with the link matrix u already in registers
-template <int P, int MU>
-__device__ __forceinline__ void hop_term_u(Spinor<typename Prec<P>::acc>& acc,
-                                           const Spinor<typename Prec<P>::acc>& psi,
-                                           const cx<typename Prec<P>::acc> (&u)[9],
-                                           typename Prec<P>::acc sgn) {
-  using A = typename Prec<P>::acc;
-  cx<A> h[2][3];
+// the projected upper half-spinor h = psi_up + sgn * B_mu psi_dn
+template <typename A, int MU>
+__device__ __forceinline__ void project_half(cx<A> (&h)[2][3], const Spinor<A>& psi, A sgn) {
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     const cx<A> p0 = psi.c[a], p1 = psi.c[3 + a], p2 = psi.c[6 + a], p3 = psi.c[9 + a];
@@ -257,6 +252,17 @@ __device__ __forceinline__ void hop_term_u(Spinor<typename Prec<P>::acc>& acc,
     h[0][a] = {p0.x + sgn * b0.x, p0.y + sgn * b0.y};
     h[1][a] = {p1.x + sgn * b1.x, p1.y + sgn * b1.y};
   }
+}
+
+// the same term with the link matrix u already in registers
+template <int P, int MU>
+__device__ __forceinline__ void hop_term_u(Spinor<typename Prec<P>::acc>& acc,
+                                           const Spinor<typename Prec<P>::acc>& psi,
+                                           const cx<typename Prec<P>::acc> (&u)[9],
+                                           typename Prec<P>::acc sgn) {
+  using A = typename Prec<P>::acc;
+  cx<A> h[2][3];
+  project_half<A, MU>(h, psi, sgn);
   cx<A> g[2][3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {

@@ -171,6 +171,11 @@ __host__ __device__ constexpr bool gather_ring(int g) {
   return g == G_RING || g == G_RING_BPF || g == G_RING_TMA;
 }
 __host__ __device__ constexpr bool gather_tma(int g) { return g == G_TMA || g == G_RING_TMA; }
+// Slice mode of a stage launch: one fifth-dimension slice per thread, or two (slices w and
+// w + Ls/2, each link read once for both; FP32 with the links in shared memory), the latter
+// also with the two slices' components packed in float2 and f32x2 arithmetic.
+enum SliceMode { SP_ONE = 1, SP_PAIR = 2, SP_PAIR_F2 = 3 };
+__host__ __device__ constexpr int slices_per_thread(int sp) { return sp == SP_ONE ? 1 : 2; }
 // bulk-prefetch depth of a gather mode: 0 none, 1 links, 2 links and streamed inputs
 __host__ __device__ constexpr int bpf_what(int g) {
   return g == G_BPF_LS ? 2 : g == G_BPF_L ? 1 : g == G_RING_BPF ? 2 : 0;
@@ -534,8 +539,132 @@ __device__ __forceinline__ void hop_pair(Spinor<typename Prec<P>::acc> (&acc)[2]
   hop_pair_d<P, 7, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
 }
 
-// SP: slices per thread (1, or 2 for the FP32 paired-slice variant: thread (lane, w) computes
-// slices w and w + Ls/2 and loads each link once for both).
+// Packed paired-slice hop (FP32): component k of slices w and w + lsp shares one float2, so
+// each f32x2 add or fma does the work of two FP32 instructions.  The projection to the
+// half-spinor is done per slice (its results pair up in registers); the SU(3) products, with
+// each link element broadcast to both halves, and the reconstruction run on the pairs.
+struct cx2 {
+  float2 x, y;   // real parts of the two slices, imaginary parts
+};
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+
+template <int MU>
+__device__ __forceinline__ void hop_term_f2(cx2 (&acc)[12], const Spinor<float>& psi0,
+                                            const Spinor<float>& psi1, const cx<float> (&u)[9],
+                                            float sgn) {
+  cx<float> h0[2][3], h1[2][3];
+  project_half<float, MU>(h0, psi0, sgn);
+  project_half<float, MU>(h1, psi1, sgn);
+  cx2 h[2][3];
+#pragma unroll
+  for (int i = 0; i < 2; i++)
+#pragma unroll
+    for (int b = 0; b < 3; b++)
+      h[i][b] = {make_float2(h0[i][b].x, h1[i][b].x), make_float2(h0[i][b].y, h1[i][b].y)};
+  const float2 m1 = bcast2(-1.f);
+  cx2 g[2][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const float2 ux0 = bcast2(u[3 * a].x), uy0 = bcast2(u[3 * a].y);
+    const float2 ux1 = bcast2(u[3 * a + 1].x), uy1 = bcast2(u[3 * a + 1].y);
+    const float2 ux2 = bcast2(u[3 * a + 2].x), uy2 = bcast2(u[3 * a + 2].y);
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+      // re: sum u.x h.x - sum u.y h.y;  im: sum u.x h.y + sum u.y h.x
+      float2 re = __fmul2_rn(ux0, h[i][0].x);
+      re = __ffma2_rn(ux1, h[i][1].x, re);
+      re = __ffma2_rn(ux2, h[i][2].x, re);
+      float2 q = __fmul2_rn(uy0, h[i][0].y);
+      q = __ffma2_rn(uy1, h[i][1].y, q);
+      q = __ffma2_rn(uy2, h[i][2].y, q);
+      float2 im = __fmul2_rn(ux0, h[i][0].y);
+      im = __ffma2_rn(ux1, h[i][1].y, im);
+      im = __ffma2_rn(ux2, h[i][2].y, im);
+      im = __ffma2_rn(uy0, h[i][0].x, im);
+      im = __ffma2_rn(uy1, h[i][1].x, im);
+      im = __ffma2_rn(uy2, h[i][2].x, im);
+      g[i][a] = {__ffma2_rn(q, m1, re), im};
+    }
+  }
+  // acc += v (s > 0) or acc -= v (s < 0): multiplying by -1 is exact, so the fma rounds once
+  // like a subtraction
+  auto add = [&](float2& acc_, float2 v, bool neg) {
+    acc_ = neg ? __ffma2_rn(v, m1, acc_) : __fadd2_rn(acc_, v);
+  };
+  const bool sn = sgn < 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    add(acc[a].x, g[0][a].x, false);
+    add(acc[a].y, g[0][a].y, false);
+    add(acc[3 + a].x, g[1][a].x, false);
+    add(acc[3 + a].y, g[1][a].y, false);
+    // lower spins: sgn * B^dag g, B^dag as in hop_term_u (i z = (-z.y, z.x))
+    if constexpr (MU == 0) {          // l0 = i g1, l1 = i g0
+      add(acc[6 + a].x, g[1][a].y, !sn);
+      add(acc[6 + a].y, g[1][a].x, sn);
+      add(acc[9 + a].x, g[0][a].y, !sn);
+      add(acc[9 + a].y, g[0][a].x, sn);
+    } else if constexpr (MU == 1) {   // l0 = g1, l1 = -g0
+      add(acc[6 + a].x, g[1][a].x, sn);
+      add(acc[6 + a].y, g[1][a].y, sn);
+      add(acc[9 + a].x, g[0][a].x, !sn);
+      add(acc[9 + a].y, g[0][a].y, !sn);
+    } else if constexpr (MU == 2) {   // l0 = i g0, l1 = -i g1
+      add(acc[6 + a].x, g[0][a].y, !sn);
+      add(acc[6 + a].y, g[0][a].x, sn);
+      add(acc[9 + a].x, g[1][a].y, sn);
+      add(acc[9 + a].y, g[1][a].x, !sn);
+    } else {                          // l0 = g0, l1 = g1
+      add(acc[6 + a].x, g[0][a].x, sn);
+      add(acc[6 + a].y, g[0][a].y, sn);
+      add(acc[9 + a].x, g[1][a].x, sn);
+      add(acc[9 + a].y, g[1][a].y, sn);
+    }
+  }
+}
+
+template <int D, bool DAG, bool BLOCKED>
+__device__ __forceinline__ void hop_pair_f2_d(cx2 (&acc)[12], const StageArgs& a, long site,
+                                              int lane, int w, int lsp, const uint4* lsm) {
+  const uint32_t nb = __ldg(a.nbr + (long)D * a.Vp + site);
+  const void* src;
+  long vs;
+  if (!nbr_source<BLOCKED>(a, nb, src, vs)) return;
+  const long j = (long)(nb & NBR_IDX);
+  constexpr bool back = (D & 1) != 0;
+  constexpr float sgn = (back != DAG) ? 1.f : -1.f;
+  Spinor<float> psi0, psi1;
+  load_spinor<P32>(psi0, src, vs, j, w);
+  load_spinor<P32>(psi1, src, vs, j, w + lsp);
+  cx<float> u[9];
+  load_link9<P32, true>(u, lsm, 32, lane, D);
+  hop_term_f2<D / 2>(acc, psi0, psi1, u, sgn);
+}
+
+template <bool DAG, bool BLOCKED>
+__device__ __forceinline__ void hop_pair_f2(Spinor<float> (&out)[2], const StageArgs& a,
+                                            long site, int lane, int w, int lsp,
+                                            const uint4* lsm) {
+  cx2 acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; k++) acc[k] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  hop_pair_f2_d<0, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_f2_d<1, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_f2_d<2, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_f2_d<3, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_f2_d<4, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_f2_d<5, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_f2_d<6, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_f2_d<7, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    out[0].c[k] = {acc[k].x.x, acc[k].y.x};
+    out[1].c[k] = {acc[k].x.y, acc[k].y.y};
+  }
+}
+
+// SP: slice mode (enum SliceMode).  In the paired modes thread (lane, w) computes slices w and
+// w + Ls/2 and loads each link once for both.
 template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G, int SP = 1>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
                                            unsigned char* smem_raw, double* red_scratch,
@@ -545,8 +674,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   using A = typename Prec<P>::acc;
   const int lane = threadIdx.x, w = threadIdx.y;
   const int tid = lane + 32 * w;
-  constexpr int NT = 32 * LS / SP;
-  constexpr int LSP = LS / SP;   // distance between a thread's slices
+  constexpr int NSL = slices_per_thread(SP);
+  constexpr int NT = 32 * LS / NSL;
+  constexpr int LSP = LS / NSL;   // distance between a thread's slices
   const long site = tile * 32 + lane;
   int seg, ntl, jl, vh;
   long first;
@@ -573,9 +703,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   // this tile's fifth-dimension coefficients (per problem when batched), read where used
   auto K5 = [&]() -> Coef5<A> { return a.tile_seg ? coef5<A>(a.segp[seg]) : coef5<A>(a); };
 
-  Spinor<A> acc[SP];
+  Spinor<A> acc[NSL];
 #pragma unroll
-  for (int j = 0; j < SP; j++) zero(acc[j]);
+  for (int j = 0; j < NSL; j++) zero(acc[j]);
   // G_TMA / G_RING_TMA: stage the tile's links in shared memory (after the ring / post area)
   const uint4* lsm = nullptr;
   if constexpr (gather_tma(G)) {
@@ -592,7 +722,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     lk_phase ^= 1u;
     lsm = reinterpret_cast<const uint4*>(lk);
   }
-  if constexpr (SP == 1) {
+  if constexpr (SP == SP_ONE) {
     const int s = w;
     if constexpr (gather_ring(G)) {
       if constexpr (G == G_RING_BPF) prefetch_tile<P, LS, BLOCKED, 2>(a, tile);
@@ -632,20 +762,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
   } else {
     // paired slices (FP32, links staged in shared memory): one link load serves both slices
-    static_assert(SP == 1 || gather_tma(G), "paired slices read the links from shared memory");
+    static_assert(gather_tma(G), "paired slices read the links from shared memory");
+    static_assert(SP != SP_PAIR_F2 || P == P32, "packed pairs are FP32 only");
     if (valid) {
-      if constexpr (SP == 2) hop_pair<P, DAG, BLOCKED>(acc, a, site, lane, w, LSP, lsm);
+      if constexpr (SP == SP_PAIR) hop_pair<P, DAG, BLOCKED>(acc, a, site, lane, w, LSP, lsm);
+      if constexpr (SP == SP_PAIR_F2) hop_pair_f2<DAG, BLOCKED>(acc, a, site, lane, w, LSP, lsm);
     }
   }
 
-  if constexpr (POST == 2 && (P == P16 || P == PB16) && SP == 1) {
+  if constexpr (POST == 2 && (P == P16 || P == PB16) && SP == SP_ONE) {
     post_tensor_core<LS>(acc[0], a, lane, w, tid, smem_raw, tc_mbar, tc_slot, tc_phase);
   }
   if constexpr (POST == 3) {
     // D+^dag h at s = b h_s + c (P+ h_{s+1} + P- h_{s-1}),  h_{Ls} = -mf h_0, h_{-1} = -mf h_{Ls-1}
     A* buf = reinterpret_cast<A*>(smem_raw);
 #pragma unroll
-    for (int j = 0; j < SP; j++)
+    for (int j = 0; j < NSL; j++)
 #pragma unroll
       for (int k = 0; k < 12; k++) {
         buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane] = acc[j].c[k].x;
@@ -655,7 +787,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     const Coef5<A> C = K5();
     const A b_ = C.db, c_ = C.dc;
 #pragma unroll
-    for (int j = 0; j < SP; j++) {
+    for (int j = 0; j < NSL; j++) {
       const int s = w + j * LSP;
       const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
       const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
@@ -677,7 +809,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     //   upper: mirror image, kappa = r mf / (1 + mf (-r)^Ls);  M5op^-1 v = z / alpha.
     A* buf = reinterpret_cast<A*>(smem_raw);
 #pragma unroll
-    for (int j = 0; j < SP; j++)
+    for (int j = 0; j < NSL; j++)
 #pragma unroll
       for (int k = 0; k < 12; k++) {
         buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane] = acc[j].c[k].x;
@@ -741,7 +873,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < SP; j++)
+    for (int j = 0; j < NSL; j++)
 #pragma unroll
       for (int k = 0; k < 12; k++) {
         acc[j].c[k].x = buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane];
@@ -756,7 +888,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     const A* pm = reinterpret_cast<const A*>(post);
     for (int i = tid; i < 2 * LS * LS; i += NT) mat[i] = pm[i];
 #pragma unroll
-    for (int j = 0; j < SP; j++)
+    for (int j = 0; j < NSL; j++)
 #pragma unroll
       for (int k = 0; k < 12; k++) {
         buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane] = acc[j].c[k].x;
@@ -779,7 +911,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     }
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < SP; j++)
+    for (int j = 0; j < NSL; j++)
 #pragma unroll
       for (int k = 0; k < 12; k++) {
         acc[j].c[k].x = buf[((w + j * LSP) * 24 + 2 * k) * 32 + lane];
@@ -789,7 +921,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
 
   A nrm = A(0);   // this thread's share of the reduction, in the accumulation type
 #pragma unroll
-  for (int jj = 0; jj < SP; jj++) {
+  for (int jj = 0; jj < NSL; jj++) {
     const int s = w + jj * LSP;
     Spinor<A>& acc_j = acc[jj];
     A hs;
@@ -855,9 +987,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
 
 // MINB = resident CTAs per SM the register budget is sized for (2 or 3); the launcher's
 // autotuner picks the faster one per kernel configuration.
-// G: how the neighbours are gathered (enum Gather); SP: slices per thread (block 32 x Ls/SP).
+// G: how the neighbours are gathered (enum Gather); SP: slice mode (enum SliceMode; block
+// 32 x Ls / slices per thread).
 template <int P, int LS, bool DAG, bool BLOCKED, int POST, int MINB, int G, int SP = 1>
-__global__ void __launch_bounds__(32 * LS / SP, MINB) stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(32 * LS / slices_per_thread(SP), MINB) stage_kernel(const StageArgs a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ double red_scratch[32];
   __shared__ uint64_t tc_mbar;

@@ -32,7 +32,7 @@ static cudaError_t stage_launch_v(const StageArgs& b, size_t sm, long g, cudaStr
     if (e != cudaSuccess) return e;
     attr_set.fetch_or(bit);
   }
-  k<<<dim3((unsigned)g), dim3(32, LS / SP), sm, st>>>(b);
+  k<<<dim3((unsigned)g), dim3(32, LS / slices_per_thread(SP)), sm, st>>>(b);
   return cudaGetLastError();
 }
 
@@ -99,8 +99,11 @@ static void stage_cands(StageCand* c, int& n) {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA>(c, n, 2);
     // two slices per thread, one link load for both (half the warps, twice the loads each)
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, 2>(c, n, 0);
-    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, 2>(c, n, 2);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, SP_PAIR>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, SP_PAIR>(c, n, 2);
+    // the same with the pairs packed in float2 (f32x2 arithmetic)
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, SP_PAIR_F2>(c, n, 0);
+    stage_cand<P, LS, DAG, BLK, POST, 2, G_TMA, SP_PAIR_F2>(c, n, 2);
   } else {
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 0);
     stage_cand<P, LS, DAG, BLK, POST, 2, G_REG>(c, n, 2);

@@ -164,7 +164,7 @@ def test_post_by_matrix_and_by_recurrence(case, prec, mode, monkeypatch):
         assert rel(host(out), ref) <= TOL[prec], (op, rel(host(out), ref))
 
 
-@pytest.mark.parametrize("variant", [str(i) for i in range(7)])
+@pytest.mark.parametrize("variant", [str(i) for i in range(9)])
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16"])
 def test_every_launch_variant_matches_oracle(variant, prec, monkeypatch):
     """Every compiled launch variant of the stages (register budget, grid, link staging,
