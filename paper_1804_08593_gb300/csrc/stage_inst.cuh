@@ -61,12 +61,14 @@ struct StageTune {
 
 // The variants timed per stage kind (the first is the default for launches that are never
 // timed).  FP32 gathers into registers, plain or after a bulk L2 prefetch of the tile's links
-// (and streamed inputs), or with the tile's links copied into shared memory by the TMA engine;
-// a register budget for 3 CTAs per SM spills, and the cp.async ring, per-direction L1
-// prefetch, prefetching the neighbour runs and prefetching the next tile of a persistent CTA
-// measured slower.  FP16/BF16 gather through the L1-cached cp.async ring with a register
-// budget for 2 or 3 CTAs per SM, with the tile's links and streams prefetched into L2 or its
-// links staged in shared memory by TMA.  FP64 (ALU bound): one CTA per tile or persistent.
+// (and streamed inputs), or with the tile's links copied into shared memory by the TMA engine,
+// with one or two fifth-dimension slices per thread; a register budget for 3 CTAs per SM
+// spills, and the cp.async ring, per-direction L1 prefetch, prefetching the neighbour runs and
+// prefetching the next tile of a persistent CTA measured slower.  FP16/BF16 gather through the
+// L1-cached cp.async ring with a register budget for 2 or 3 CTAs per SM, with the tile's links
+// and streams prefetched into L2 or its links staged in shared memory by TMA, one CTA per tile
+// (persistent grids measured 10-35 % slower there; only the tensor-core post, whose set-up is
+// per CTA, has them).  FP32 and FP64 (ALU bound): one CTA per tile or a persistent grid.
 template <int P, int LS, bool DAG, bool BLK, int POST, int MINB, int G, int SP = 1>
 static void stage_cand(StageCand* c, int& n, int per_sm) {
   c[n++] = {stage_launch_v<P, LS, DAG, BLK, POST, MINB, G, SP>,
