@@ -47,7 +47,8 @@
  * applied).  Per process, the first launches of each (stage kind, lattice size) that carry no
  * solver stop flag cycle through them timed with CUDA events, and the fastest is kept.  All
  * variants agree bit for bit except the tensor-core and recurrence forms of the 16-bit post
- * (both within the 16-bit tolerance).  Environment switches: DWF_STAGE_VARIANT=<i> forces
+ * and the packed-float2 FP32 form (another rounding order), each within its precision's
+ * tolerance.  Environment switches: DWF_STAGE_VARIANT=<i> forces
  * variant i; DWF_TUNE_LOG=1 prints each decision on stderr; DWF_POST=matrix|recurrence and
  * DWF_DISABLE_TC=1 (read by dwf_create) restrict the post forms; DWF_RU_DELTA overrides the
  * reliable-update threshold 0.1 of the mixed-precision solvers.
