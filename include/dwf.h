@@ -108,7 +108,10 @@ typedef struct {
 dwf_status dwf_create(dwf_t* handle, const int dims[4], int Ls, double M5, double mf,
                       double b, double c, const void* links, void* stream);
 
-/* Replaces the links (same layout); packed copies of every precision are refreshed. */
+/* Replaces the links (same layout, host or device; read during the call only, the caller
+ * keeps them); packed copies of every precision are rebuilt before the next use.  For gauge
+ * fields that change between solves, the ensemble-generation setting of Sec. 1.  Returns
+ * DWF_ERR_ARG for a NULL argument, DWF_ERR_CUDA if the copy fails; synchronises the stream. */
 dwf_status dwf_update_links(dwf_t handle, const void* links);
 
 /* out = op(in), computed in precision prec (in is rounded to prec first; out is written back
@@ -152,7 +155,11 @@ dwf_status dwf_mspcg(dwf_t handle, const int block[4], int inner_iters, dwf_prec
  * dS = -2 Re <Mpc X, dMpc X>, dMpc from the hopping terms of Mpc (Sec. 2.2). */
 dwf_status dwf_force(dwf_t handle, const void* phi, const void* X, void* dSdU, double tol);
 
-/* The pseudofermion action S for a solution X (or NULL: solved internally to tol). */
+/* The pseudofermion action S = phi^dag (Mpc^dag Mpc)^-1 phi whose solves the paper speeds up
+ * (Sec. 1), for a solution X (even-half complex128, host or device) or NULL (solved
+ * internally with FP64 CG to tol).  Evaluated as Re(2 <phi, X> - ||Mpc X||^2), which equals S
+ * at the exact solution and errs quadratically in the solve residual.  *S is a host double;
+ * returns DWF_ERR_ARG for a NULL handle, phi or S. */
 dwf_status dwf_action(dwf_t handle, const void* phi, const void* X, double tol, double* S);
 
 /* One problem of a batched solve. */
@@ -166,17 +173,21 @@ typedef struct {
 } dwf_problem;
 
 /* Solves n independent problems A_i x_i = phi_i (each its own lattice, Ls and masses) to tol
- * with FP32 CG and FP64 reliable updates.  All problems advance together: every CG step of
- * every problem runs in one persistent kernel launch, and the whole step sequence is a
- * captured CUDA graph.  stream: cudaStream_t.  per_solve (n entries, nullable) receives
- * each problem's statistics. */
+ * with FP32 CG and FP64 reliable updates (the CG of Eq. 3 per problem; batching many solves
+ * has no counterpart in the paper).  All problems advance together: every CG step of every
+ * problem runs in one persistent kernel launch, and the whole step sequence is a captured
+ * CUDA graph.  stream: cudaStream_t.  per_solve (n entries, nullable) receives each
+ * problem's statistics.  Fields are host or device; the call keeps none of the caller's
+ * pointers.  Returns DWF_ERR_ARG for n <= 0, a bad tolerance, an unsupported size or a NULL
+ * field, DWF_ERR_NOT_CONVERGED if some problem misses tol within maxit steps. */
 dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double tol, int maxit,
                            dwf_stats* per_solve, void* stream);
 
-/* Per-kernel timing of one handle.  While enabled, every kernel launch of the handle is
- * bracketed by CUDA events on the handle's stream and its algorithmic HBM bytes are recorded
- * (reads of every input and write of every output once, links once per site).  dwf_profile_read
- * synchronises the stream, sums the event times per kernel class and resets the counters. */
+/* Per-kernel timing of one handle (instrumentation; no counterpart in the paper).  While
+ * enabled, every kernel launch of the handle is bracketed by CUDA events on the handle's
+ * stream and its algorithmic HBM bytes are recorded (reads of every input and write of every
+ * output once, links once per site).  dwf_profile_read synchronises the stream, sums the
+ * event times per kernel class and resets the counters. */
 typedef struct {
   char name[48];              /* kernel class, e.g. "hop_f16_blocked"                     */
   int launches;
