@@ -99,6 +99,12 @@ typedef struct {
   double* history;           /* optional caller array: ||r_k||/||phi|| per outer iteration */
   int history_capacity;      /* length of history (0 = not recorded)                       */
   int history_len;           /* entries written                                            */
+  /* optional caller array (dwf_cg only; history_capacity entries, history_len written):
+   * <p_k, A p_k> / ||phi||^2 of CG iteration k.  With history it gives the CG coefficients
+   * alpha_k = rho_k / <p_k, A p_k>, beta_k = rho_{k+1} / rho_k (rho_k = ||r_k||^2), i.e. the
+   * Lanczos tridiagonal of A whose extreme eigenvalues estimate kappa(A).  Meaningful for an
+   * uninterrupted CG sequence: prec = DWF_F64 (no reliable-update restarts). */
+  double* curvature_history;
 } dwf_stats;
 
 /* Creates a handle for a lattice dims = {X, Y, Z, T} with Ls slices and operator parameters
@@ -174,9 +180,11 @@ typedef struct {
 
 /* Solves n independent problems A_i x_i = phi_i (each its own lattice, Ls and masses) to tol
  * with FP32 CG and FP64 reliable updates (the CG of Eq. 3 per problem; batching many solves
- * has no counterpart in the paper).  All problems advance together: every CG step of every
- * problem runs in one persistent kernel launch, and the whole step sequence is a captured
- * CUDA graph.  stream: cudaStream_t.  per_solve (n entries, nullable) receives each
+ * has no counterpart in the paper).  All problems advance together: problems with the same
+ * Ls share one concatenated site space, and one CG step of all of them is five kernel
+ * launches per Ls group (stages A, B, A^dag, B^dag on persistent grids, then the update);
+ * chunks of 16 steps of all groups are captured once as a CUDA graph and replayed, with the
+ * per-problem FP64 reliable updates between replays.  stream: cudaStream_t.  per_solve (n entries, nullable) receives each
  * problem's statistics.  Fields are host or device; the call keeps none of the caller's
  * pointers.  Returns DWF_ERR_ARG for n <= 0, a bad tolerance, an unsupported size or a NULL
  * field, DWF_ERR_NOT_CONVERGED if some problem misses tol within maxit steps. */
@@ -218,6 +226,27 @@ dwf_status dwf_profile_read(dwf_t handle, dwf_kernel_profile* out, int capacity,
 dwf_status dwf_mdagm_noalloc(const int dims[4], int Ls, double M5, double mf, double b,
                              double c, const void* links, const void* in, void* out,
                              dwf_prec prec, void* stream);
+
+/* Per-handle options (failure detection; no counterpart in the paper).
+ *   DWF_OPT_WAIT_LIMIT_US: time limit, in microseconds (1 .. 1e7), of every bounded device-side
+ *     wait of the handle's kernels (TMA link staging, tensor-core completion); default 10 ms.
+ *     A wait that runs out makes the call return DWF_ERR_TIMEOUT (its output is not valid);
+ *     the handle stays usable.
+ *   DWF_OPT_TEST_WAIT_PROBE: value != 0 makes every FP32/FP16/BF16 operator stage of the handle
+ *     run its TMA link-staging variant without issuing the copies, so the wait on the
+ *     copies' mbarrier cannot complete and runs out: the call returns DWF_ERR_TIMEOUT with
+ *     nothing left in flight.  For tests of the timeout path only; FP64 stages (which have no
+ *     such variant) fail with DWF_ERR_CUDA while it is set.
+ * Returns DWF_ERR_ARG for a NULL handle, an unknown option or a value out of range. */
+typedef enum { DWF_OPT_WAIT_LIMIT_US = 0, DWF_OPT_TEST_WAIT_PROBE = 1 } dwf_option;
+dwf_status dwf_set_option(dwf_t handle, dwf_option option, double value);
+
+/* Measures a peak arithmetic rate of the current device (measurement support for the
+ * rooflines; no counterpart in the paper): which = 0 FP64 fused multiply-add (DFMA), 1 FP32
+ * (FFMA).  Runs a short kernel of independent FMA chains on every SM, timed with CUDA events
+ * on stream (cudaStream_t), and writes the rate in TFLOP/s (2 flops per FMA) to *tflops.  No
+ * clock or power setting is touched.  Returns DWF_ERR_ARG for a bad `which` or NULL tflops. */
+dwf_status dwf_measure_peak(int which, void* stream, double* tflops);
 
 /* Thread-local description of the last error (never NULL). */
 const char* dwf_last_error(void);

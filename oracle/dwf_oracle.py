@@ -29,10 +29,10 @@ What the paper fixes and what is a reading (the paper does not print the operato
     Mpc = M5op - 1/4 Dh_eo D+ M5op^-1 Dh_oe D+,   A = Mpc^dag Mpc, solved as A x = phi.
 * MSPCG (Sec. 2.3, Eqs. 4-5): preconditioned CG whose preconditioner is M = direct sum of the
   block-diagonal pieces A_s, applied as l plain CG iterations per block from a zero guess.
-  Two readings of A_s: local_op="exact" is P_s A P_s, the diagonal block of A itself (the
-  paper's "same local block diagonal entries with A"); local_op="drop" is Mpc^dag Mpc built
-  with every link whose two ends lie in different blocks set to zero (hopping across block
-  faces dropped).  beta is Fletcher-Reeves unless flexible=True (Polak-Ribiere).
+  Two readings of A_s: local_op="exact" is P_s A P_s, the diagonal block of A itself (Eq. 5:
+  M keeps the diagonal blocks of A and has zero off-diagonal blocks); local_op="drop" is
+  Mpc^dag Mpc built with every link whose two ends lie in different blocks set to zero
+  (hopping across block faces dropped).  beta is Fletcher-Reeves unless flexible=True (Polak-Ribiere).
 
 Every function here is pinned by a test in tests/test_oracle.py (no function is unpinned).
 * Cost arithmetic of Sec. 4.1, Eqs. 6-7.
@@ -444,8 +444,8 @@ def block_cg(apply_ablk, r: np.ndarray, eb: np.ndarray, nblocks: int, iters: int
 
 
 def exact_block_operator(U: np.ndarray, p: DWFParams, block):
-    """A_s = P_s A P_s for every block at once (the paper's M: 'the same local block
-    diagonal entries with A', Sec. 2.3 Eq. 5).  Applied block by block: the vector is
+    """A_s = P_s A P_s for every block at once: the block-diagonal part of A, which is what
+    the preconditioner M of Sec. 2.3, Eq. 5 is made of.  Applied block by block: the vector is
     restricted to one block, A is applied, and the result is restricted to the same block."""
     eb = even_block_ids(p.dims, block)
     nblocks = int(np.prod([p.dims[i] // block[i] for i in range(4)]))

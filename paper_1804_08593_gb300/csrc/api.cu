@@ -81,8 +81,16 @@ dwf_status check_device_error(dwf_ctx* h) {
   DWF_CUDA(cudaMemcpyAsync(&e, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DWF_CUDA(cudaStreamSynchronize(h->stream));
   if (e) {
+    // a CTA that gave up left its reduction segment unfinished: clear the counters so the
+    // handle's next reductions start from zero
     DWF_CUDA(cudaMemsetAsync(h->dev_err, 0, sizeof(int), h->stream));
-    return set_error(DWF_ERR_TIMEOUT, "a bounded device-side wait (tensor-core completion) gave up");
+    if (h->red_counter)
+      DWF_CUDA(cudaMemsetAsync(h->red_counter, 0, h->red_counter_len * sizeof(unsigned),
+                               h->stream));
+    DWF_CUDA(cudaStreamSynchronize(h->stream));
+    return set_error(DWF_ERR_TIMEOUT,
+                     "a bounded device-side wait (TMA link staging or tensor-core completion) "
+                     "gave up");
   }
   return DWF_OK;
 }
@@ -99,7 +107,23 @@ extern "C" {
 
 const char* dwf_last_error(void) { return g_last_error.c_str(); }
 
-const char* dwf_version(void) { return "dwf-gb300 0.1 (sm_103a)"; }
+const char* dwf_version(void) { return "dwf-gb300 0.2 (sm_103a)"; }
+
+dwf_status dwf_set_option(dwf_t h, dwf_option opt, double value) {
+  if (!h) return set_error(DWF_ERR_ARG, "null handle");
+  switch (opt) {
+    case DWF_OPT_WAIT_LIMIT_US:
+      if (!(value >= 1.0 && value <= 1e7))
+        return set_error(DWF_ERR_ARG, "wait limit must be in [1, 1e7] microseconds");
+      h->wait_ns = (unsigned long long)(value * 1000.0);
+      return DWF_OK;
+    case DWF_OPT_TEST_WAIT_PROBE:
+      h->wait_probe = value != 0.0 ? 1 : 0;
+      return DWF_OK;
+    default:
+      return set_error(DWF_ERR_ARG, "unknown option");
+  }
+}
 
 dwf_status dwf_create(dwf_t* handle, const int dims[4], int Ls, double M5, double mf, double b,
                       double c, const void* links, void* stream) {

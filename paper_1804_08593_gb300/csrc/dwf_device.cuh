@@ -338,7 +338,7 @@ struct RedArgs {
   const double* stop2;  // per-segment stop threshold on v, nullable
   int* conv;            // conv[seg] set to 1 when v <= stop2[seg], nullable
   const double* extra;  // FIN_ALPHA2: partial sum from a previous launch
-  double* hist;         // FIN_BETA: hist[*hist_idx] = v (nullable)
+  double* hist;         // FIN_BETA: hist[*hist_idx] = v; FIN_ALPHA: the curvature (nullable)
   const int* hist_idx;
   int hist_cap;
 };
@@ -384,6 +384,7 @@ __device__ void finalize_value(const RedArgs& r, int seg, const double (&v)[NV])
     const double rho = r.rho[seg];
     const double pap = r.op == FIN_ALPHA2 ? x + r.extra[seg] : x;
     r.alpha[seg] = (pap > 0.0 && isfinite(pap)) ? rho / pap : 0.0;
+    if (r.hist && *r.hist_idx < r.hist_cap) r.hist[*r.hist_idx] = pap;
   } else if (r.op == FIN_BETA) {
     const double rho = r.rho[seg];
     r.beta[seg] = (rho > 0.0 && isfinite(x)) ? x / rho : 0.0;

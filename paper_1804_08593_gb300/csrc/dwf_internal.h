@@ -183,6 +183,8 @@ struct dwf_ctx {
   size_t scal_len = 0;
   double* h_pinned = nullptr;  // pinned host mirror for scalar reads
   int* dev_err = nullptr;      // set by a bounded device wait that gave up
+  unsigned long long wait_ns = 0;  // limit of bounded device waits (0: the kernels' 10 ms)
+  int wait_probe = 0;              // failure-detection test switch (see dwf_set_option)
   dwf::Profiler prof;
 };
 

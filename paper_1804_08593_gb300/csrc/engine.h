@@ -90,6 +90,8 @@ struct OpEngine {
     a.l_beta = h->mats.m5_beta;
     a.seg_cps = seg_cps;
     a.err = h->dev_err;
+    a.wait_ns = h->wait_ns;
+    a.wait_probe = h->wait_probe;
     return a;
   }
   dwf_status launch(const StageArgs& a, bool dag) const {

@@ -14,7 +14,9 @@
 // (with that device current) looks the address up once with cudaGetSymbolAddress and caches
 // it; make that first call before any stream capture.  All calls share the array and leave
 // their data in it; calls whose executions overlap on the GPU (different streams, or the same
-// stream from several host threads) race on it and must be serialised by the caller.
+// stream from several host threads) race on it and must be serialised by the caller.  The
+// fifth-dimension matrices reach the device as a kernel argument (no host buffer outlives the
+// call), and a bounded device wait that gives up turns the whole output into NaN.
 #include <mutex>
 #include <vector>
 
@@ -93,6 +95,32 @@ __global__ void plain_tables_kernel(int X, int Y, int Z, int T, long Vh, long Vp
 
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
+// The three per-chirality fifth-dimension matrices ([3][2][Ls][Ls], Ls <= 16) travel to the
+// device inside the kernel's parameter block, so no host buffer is read after the call
+// returns and no host-to-device copy is queued.
+struct MatParam {
+  double v[3 * 2 * 16 * 16];
+};
+static_assert(sizeof(MatParam) <= 32000, "kernel parameter block limit");
+
+__global__ void write_mats_kernel(const MatParam m, int n, int as_double, void* dst) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (as_double) static_cast<double*>(dst)[i] = m.v[i];
+    else static_cast<float*>(dst)[i] = (float)m.v[i];
+  }
+}
+
+// A bounded device wait that gave up (TMA link staging, tensor-core completion) sets *status;
+// then every element of the output becomes a quiet NaN, so that a timed-out call cannot pass
+// for a valid result (the call itself returns before the kernels run).
+__global__ void poison_if_error_kernel(const int* status, double* out, long n) {
+  if (*status == 0) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x)
+    out[i] = nan;
+}
+
 }  // namespace
 }  // namespace dwf
 
@@ -135,6 +163,7 @@ extern "C" dwf_status dwf_mdagm_noalloc(const int dims[4], int Ls, double M5, do
   const size_t o_lex0 = take(Vp * 4), o_lex1 = take(Vp * 4), o_cbe = take(Vp * 4);
   const size_t o_l0 = take(8 * link_chunks * 16 * Vp), o_l1 = take(8 * link_chunks * 16 * Vp);
   const size_t o_m = take(3 * 2 * Ls * Ls * acc);
+  const size_t o_status = take(sizeof(int));
   size_t o_f[6];
   for (int i = 0; i < 6; i++) o_f[i] = take(fb);
   if (off > kScratchBytes)
@@ -149,19 +178,16 @@ extern "C" dwf_status dwf_mdagm_noalloc(const int dims[4], int Ls, double M5, do
   double ma, mb;
   if (!fifth_dim_matrices(Ls, M5, mf, b, c, dpm5i, m5idpt, dpt, &ma, &mb))
     return set_error(DWF_ERR_ARG, "M5op is singular");
-  std::vector<unsigned char> mats(3 * 2 * Ls * Ls * acc);
+  MatParam mp;
   for (int w = 0; w < 3; w++) {
     const std::vector<double>& m = w == 0 ? dpm5i : w == 1 ? m5idpt : dpt;
-    for (int i = 0; i < 2 * Ls * Ls; i++) {
-      if (acc == sizeof(double)) {
-        reinterpret_cast<double*>(mats.data())[w * 2 * Ls * Ls + i] = m[i];
-      } else {
-        reinterpret_cast<float*>(mats.data())[w * 2 * Ls * Ls + i] = (float)m[i];
-      }
-    }
+    for (int i = 0; i < 2 * Ls * Ls; i++) mp.v[w * 2 * Ls * Ls + i] = m[i];
   }
-  // pageable source: staged by the runtime before the call returns
-  DWF_CUDA(cudaMemcpyAsync(S + o_m, mats.data(), mats.size(), cudaMemcpyHostToDevice, st));
+  write_mats_kernel<<<1, 256, 0, st>>>(mp, 3 * 2 * Ls * Ls, acc == sizeof(double) ? 1 : 0,
+                                       S + o_m);
+  DWF_CUDA(cudaGetLastError());
+  int* status = reinterpret_cast<int*>(S + o_status);
+  DWF_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
 
   uint32_t* nbr[2] = {reinterpret_cast<uint32_t*>(S + o_nbr0), reinterpret_cast<uint32_t*>(S + o_nbr1)};
   int* lex[2] = {reinterpret_cast<int*>(S + o_lex0), reinterpret_cast<int*>(S + o_lex1)};
@@ -197,6 +223,7 @@ extern "C" dwf_status dwf_mdagm_noalloc(const int dims[4], int Ls, double M5, do
     a.l_alpha = ma;
     a.l_beta = mb;
     a.epi = EPI_STORE;
+    a.err = status;
     return a;
   };
   // fields: f0 = x, f1 = D+ x, f2 = t (odd), f3 = y = Mpc x, f4 = s (odd), f5 = A x
@@ -246,5 +273,8 @@ extern "C" dwf_status dwf_mdagm_noalloc(const int dims[4], int Ls, double M5, do
   }
   DWF_CUDA(launch_stage_prec(P, s4, Ls, true, false, st));
   DWF_CUDA(launch_unpack_field_to(P, f[5], out, cbe, Vp, Vh, Ls, st));
+  poison_if_error_kernel<<<64, 256, 0, st>>>(status, static_cast<double*>(out),
+                                             (long)Ls * Vh * 24);
+  DWF_CUDA(cudaGetLastError());
   return DWF_OK;
 }

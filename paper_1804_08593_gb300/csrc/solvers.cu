@@ -169,11 +169,14 @@ struct CGVectors {
 
 // One CG iteration on the low-precision engine E; all scalars stay on the device.
 static dwf_status cg_iteration(const OpEngine& E, const CGVectors& v, double* dsc, int* dfl,
-                               double* hist, int hist_cap) {
+                               double* hist, double* curv, int hist_cap) {
   const int* stop = dfl + F_STOP;
   RedArgs ra = E.red(FIN_ALPHA, dsc + S_PAP);
   ra.rho = dsc + S_RHO;
   ra.alpha = dsc + S_ALPHA;
+  ra.hist = curv;   // <p, A p> of this iteration (Lanczos coefficients)
+  ra.hist_idx = dfl + F_ITER;
+  ra.hist_cap = curv ? hist_cap : 0;
   DWF_TRY(E.mpc(v.p, v.u, v.t, v.y, EPI_NORM, ra, stop, true));
   RedArgs rb = E.red(FIN_BETA, nullptr);
   rb.rho = dsc + S_RHO;
@@ -236,11 +239,14 @@ static dwf_status run_cg(dwf_ctx* h, Layout* lay, const void* b_c128, void* x_c1
   double* dsc;
   int* dfl;
   double* dhist = nullptr;
+  double* dcurv = nullptr;
   DWF_TRY(h->ws->get("cg_scal", S_NSLOT * sizeof(double), (void**)&dsc));
   DWF_TRY(h->ws->get("cg_flag", F_NFLAG * sizeof(int), (void**)&dfl));
   const int hcap = (stats && stats->history && stats->history_capacity > 0)
                        ? stats->history_capacity : 0;
   if (hcap) DWF_TRY(h->ws->get("cg_hist", (size_t)hcap * sizeof(double), (void**)&dhist));
+  if (hcap && stats->curvature_history)
+    DWF_TRY(h->ws->get("cg_curv", (size_t)hcap * sizeof(double), (void**)&dcurv));
 
   DWF_TRY(pack_even(h, lay, b_c128, b64, P64, 1.0));
   if (x0) DWF_TRY(pack_even(h, lay, x_c128, x64, P64, 1.0));
@@ -314,6 +320,7 @@ static dwf_status run_cg(dwf_ctx* h, Layout* lay, const void* b_c128, void* x_c1
       if (n <= 0) break;
       for (int k = 0; k < n; k++)
         DWF_TRY(cg_iteration(E, v, dsc, dfl, dhist ? dhist + total_hist : nullptr,
+                             dcurv ? dcurv + total_hist : nullptr,
                              dhist ? hcap - total_hist : 0));
       double rho;
       DWF_TRY(read_ints(h, dfl, F_NFLAG, fl));
@@ -356,6 +363,11 @@ static dwf_status run_cg(dwf_ctx* h, Layout* lay, const void* b_c128, void* x_c1
       // hist holds the low-precision ||r||^2 in scaled units; report relative norms
       for (int i = 0; i < n; i++) stats->history[i] = std::sqrt(hv[i] / bb) / hist_scale[i];
       stats->history_len = n;
+      if (dcurv && n) {
+        DWF_CUDA(cudaMemcpy(hv.data(), dcurv, n * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; i++)
+          stats->curvature_history[i] = hv[i] / (bb * hist_scale[i] * hist_scale[i]);
+      }
     }
     stats->seconds = timer.seconds();
   }

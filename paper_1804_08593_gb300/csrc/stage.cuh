@@ -44,6 +44,9 @@ struct StageArgs {
   const void* post_h;    // FP16/BF16 kernels: the same matrices as FP16 16x16 tensor-core
                          // operands (core-matrix layout); nullable = CUDA-core path
   int* err;              // set to 1 if a bounded device wait gives up (nullable)
+  unsigned long long wait_ns;  // limit of every bounded device wait (0: the default 10 ms)
+  int wait_probe;        // failure-detection test only: the TMA link staging issues no copy,
+                         // so its wait runs out and the stage reports a timeout
   int post_sparse;       // the post matrix is D+^dag = dp_b + dp_c K^dag: apply it sparsely
   int post_struct;       // dense post D+ M5op^-1 (dag: M5op^-dag D+^dag) by O(Ls) recurrences:
                          // 0 no, 1 yes, 2 the faster of recurrences and tensor cores (16-bit)
@@ -428,8 +431,9 @@ __device__ __forceinline__ void tc_teardown(const uint32_t* tslot) {
   if (threadIdx.y == 0) tc::tmem_dealloc(*tslot, tc::TMEM_COLS);
 }
 
+// Returns false (uniformly over the CTA) when the MMA completion wait gave up.
 template <int LS>
-__device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const StageArgs& a,
+__device__ __forceinline__ bool post_tensor_core(Spinor<float>& acc, const StageArgs& a,
                                                  int lane, int s, int tid,
                                                  unsigned char* smem, uint64_t* mbar,
                                                  uint32_t* tslot, uint32_t& phase) {
@@ -458,9 +462,15 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
                   tc::smem_desc(tc::smem_u32(Bt + (j / 3) * tc::B_BYTES)), idesc, 0u);
     tc::mma_commit(mbar);
   }
-  if (!tc::mbar_wait(mbar, phase) && a.err) atomicExch(a.err, 1);
+  bool ok = tc::mbar_wait(mbar, phase, a.wait_ns);
+  if (!ok) {
+    // the MMAs may still be running: record the error, wait once more (bounded) for them
+    if (a.err) atomicExch(a.err, 1);
+    tc::mbar_wait(mbar, phase, a.wait_ns);
+  }
   phase ^= 1u;
   tc::fence_after_sync();
+  if (__syncthreads_or(!ok)) return false;
   // warp s reads the TMEM lane quarter q = s % 4 (rows 32q..32q+31 = real cp%4 = q of every
   // tile); the warps sharing a quarter split the six tiles between them.  The staging area is
   // the gather ring, idle since the barrier after the hop.
@@ -481,6 +491,7 @@ __device__ __forceinline__ void post_tensor_core(Spinor<float>& acc, const Stage
     acc.c[k].x = Dst[(s * 24 + 2 * k) * 32 + lane];
     acc.c[k].y = Dst[(s * 24 + 2 * k + 1) * 32 + lane];
   }
+  return true;
 }
 
 // Dynamic shared memory of a stage: the gather ring or the post matrices' staging area.
@@ -665,8 +676,9 @@ __device__ __forceinline__ void hop_pair_f2(Spinor<float> (&out)[2], const Stage
 
 // SP: slice mode (enum SliceMode).  In the paired modes thread (lane, w) computes slices w and
 // w + Ls/2 and loads each link once for both.
+// Returns false (uniformly over the CTA) when a bounded wait gave up: the caller stops.
 template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G, int SP = 1>
-__device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
+__device__ __forceinline__ bool stage_tile(const StageArgs& a, long tile,
                                            unsigned char* smem_raw, double* red_scratch,
                                            uint64_t* tc_mbar, uint32_t* tc_slot,
                                            uint32_t& tc_phase, uint64_t* lk_mbar,
@@ -684,14 +696,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   if (a.tile_seg) {
     seg = __ldg(a.tile_seg + tile);
     const BatchSeg& S = a.segp[seg];
-    if (a.stop && a.stop[seg]) return;
+    if (a.stop && a.stop[seg]) return true;
     first = S.first_tile;
     ntl = S.ntiles;
     jl = (int)(tile - first) * 32 + lane;
     vh = S.Vh;
     if (POST) post = S.mat[a.post_which];
   } else {
-    if (a.stop && *a.stop) return;
+    if (a.stop && *a.stop) return true;
     const int cps = a.Vhb_pad >> 5;
     seg = (int)(tile / a.seg_cps);
     first = (long)seg * a.seg_cps;
@@ -711,15 +723,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   if constexpr (gather_tma(G)) {
     constexpr int NCHL = Prec<P>::NCHL;
     unsigned char* lk = smem_raw + tma_link_offset<P>(LS, POST, G);
-    if (tid == 0) {
+    if (tid == 0 && !a.wait_probe) {
       tc::fence_proxy_async_smem();   // earlier generic reads of the buffer come first
       mbar_expect_tx(lk_mbar, 8 * NCHL * 512);
       const uint4* L = reinterpret_cast<const uint4*>(a.links);
       for (int i = 0; i < 8 * NCHL; i++)
         bulk_g2s(lk + i * 512, L + (long)i * a.Vp_link + tile * 32, 512, lk_mbar);
     }
-    if (!tc::mbar_wait(lk_mbar, lk_phase) && a.err) atomicExch(a.err, 1);
+    bool ok = tc::mbar_wait(lk_mbar, lk_phase, a.wait_ns);
+    if (!ok) {
+      // copies issued but not landed: record the error and wait once more (bounded) so that
+      // none is in flight when the CTA leaves; with wait_probe nothing was issued
+      if (a.err) atomicExch(a.err, 1);
+      if (!a.wait_probe) tc::mbar_wait(lk_mbar, lk_phase, a.wait_ns);
+    }
     lk_phase ^= 1u;
+    if (__syncthreads_or(!ok)) return false;
     lsm = reinterpret_cast<const uint4*>(lk);
   }
   if constexpr (SP == SP_ONE) {
@@ -771,7 +790,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
   }
 
   if constexpr (POST == 2 && (P == P16 || P == PB16) && SP == SP_ONE) {
-    post_tensor_core<LS>(acc[0], a, lane, w, tid, smem_raw, tc_mbar, tc_slot, tc_phase);
+    if (!post_tensor_core<LS>(acc[0], a, lane, w, tid, smem_raw, tc_mbar, tc_slot, tc_phase))
+      return false;
   }
   if constexpr (POST == 3) {
     // D+^dag h at s = b h_s + c (P+ h_{s+1} + P- h_{s-1}),  h_{Ls} = -mf h_0, h_{-1} = -mf h_{Ls-1}
@@ -983,6 +1003,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, long tile,
     A v[1] = {nrm};
     grid_reduce_seg<1, A>(a.red, v, red_scratch, tile, seg, first, ntl);
   }
+  return true;
 }
 
 // MINB = resident CTAs per SM the register budget is sized for (2 or 3); the launcher's
@@ -1004,8 +1025,9 @@ __global__ void __launch_bounds__(32 * LS / slices_per_thread(SP), MINB) stage_k
   }
   uint32_t tc_phase = 0, lk_phase = 0;
   for (long tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    stage_tile<P, LS, DAG, BLOCKED, POST, G, SP>(a, tile, smem_raw, red_scratch, &tc_mbar,
-                                                 &tc_slot, tc_phase, &lk_mbar, lk_phase);
+    if (!stage_tile<P, LS, DAG, BLOCKED, POST, G, SP>(a, tile, smem_raw, red_scratch, &tc_mbar,
+                                                      &tc_slot, tc_phase, &lk_mbar, lk_phase))
+      break;
     __syncthreads();
   }
   if constexpr (TC) tc_teardown(&tc_slot);

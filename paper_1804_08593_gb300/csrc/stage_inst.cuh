@@ -154,6 +154,13 @@ static cudaError_t stage_launch_one(const StageArgs& a, cudaStream_t st) {
     if (b.grid > 0) return std::min<long>(b.grid, b.ntiles);
     return k.per_sm ? std::min<long>((long)k.per_sm * sm_count(), b.ntiles) : b.ntiles;
   };
+  // failure-detection probe: a variant with TMA link staging, outside the tuner (FP64 stages
+  // have none and refuse)
+  if (b.wait_probe) {
+    for (int k = 0; k < n; k++)
+      if (gather_tma(c[k].gather)) return c[k].fn(b, c[k].smem, grid_of(c[k]), st);
+    return cudaErrorNotSupported;
+  }
   // per (device, tile count, kind); handles on different host threads share it
   static std::mutex mu;
   static std::map<std::tuple<int, long, int>, StageTune> tunes;

@@ -21,7 +21,9 @@ namespace tc {
 constexpr int TILE_BYTES = 128 * 16 * 2;   // one A tile: 128 rows x 16 k, FP16
 constexpr int B_BYTES = 16 * 16 * 2;       // one B matrix: 16 n x 16 k, FP16
 constexpr uint32_t TMEM_COLS = 128;        // 6 tiles x 16 columns, rounded to a power of 2
-constexpr long long WAIT_CYCLES = 20000000;  // ~10 ms at 2 GHz: bounded mbarrier wait
+// Bounded mbarrier waits give up after a time limit set on the host (per handle; 10 ms when
+// the kernel argument is 0) and report an error flag instead of hanging.
+constexpr unsigned long long DEFAULT_WAIT_NS = 10000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -90,12 +92,21 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Nanoseconds of the device's global timer (independent of the SM clock).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Waits for phase `parity` of the mbarrier to complete, polling without blocking; gives up
-// after WAIT_CYCLES clock cycles and returns false (the caller records an error flag and the
-// kernel finishes instead of hanging).
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// after limit_ns nanoseconds (DEFAULT_WAIT_NS when 0) and returns false (the caller records an
+// error flag and the kernel finishes instead of hanging).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
+                                          unsigned long long limit_ns) {
   const uint32_t a = smem_u32(mbar);
-  const long long t0 = clock64();
+  const unsigned long long lim = limit_ns ? limit_ns : DEFAULT_WAIT_NS;
+  const unsigned long long t0 = globaltimer_ns();
   while (true) {
     uint32_t done;
     asm volatile(
@@ -104,7 +115,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(done) : "r"(a), "r"(parity) : "memory");
     if (done) return true;
-    if (clock64() - t0 > WAIT_CYCLES) return false;
+    if (globaltimer_ns() - t0 > lim) return false;
     __nanosleep(32);
   }
 }

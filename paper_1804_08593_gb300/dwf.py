@@ -27,7 +27,9 @@ LOCAL_DROP, LOCAL_EXACT = 0, 1
 # Every symbol include/dwf.h declares.
 EXPORTS = ("dwf_create", "dwf_update_links", "dwf_apply", "dwf_cg", "dwf_mspcg", "dwf_force",
            "dwf_action", "dwf_batch_solve", "dwf_last_error", "dwf_destroy", "dwf_version",
-           "dwf_profile_enable", "dwf_profile_read", "dwf_mdagm_noalloc")
+           "dwf_profile_enable", "dwf_profile_read", "dwf_mdagm_noalloc", "dwf_set_option",
+           "dwf_measure_peak")
+OPT_WAIT_LIMIT_US, OPT_TEST_WAIT_PROBE = 0, 1
 
 
 class DWFError(RuntimeError):
@@ -41,12 +43,17 @@ class Stats(ctypes.Structure):
                 ("reliable_updates", ctypes.c_int), ("operator_applications", ctypes.c_int),
                 ("true_residual", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("history", ctypes.POINTER(ctypes.c_double)), ("history_capacity", ctypes.c_int),
-                ("history_len", ctypes.c_int)]
+                ("history_len", ctypes.c_int),
+                ("curvature_history", ctypes.POINTER(ctypes.c_double))]
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("history",)}
+        d = {k: getattr(self, k) for k, _ in self._fields_
+             if k not in ("history", "curvature_history")}
         if self.history_len:
             d["history"] = [self.history[i] for i in range(self.history_len)]
+            if self.curvature_history:
+                d["curvature_history"] = [self.curvature_history[i]
+                                          for i in range(self.history_len)]
         return d
 
 
@@ -90,9 +97,12 @@ def load() -> ctypes.CDLL:
     lib.dwf_profile_enable.argtypes = [vp, i]
     lib.dwf_mdagm_noalloc.argtypes = [ctypes.POINTER(i), i, d, d, d, d, vp, vp, vp, i, vp]
     lib.dwf_profile_read.argtypes = [vp, ctypes.POINTER(KernelProfile), i, ctypes.POINTER(i)]
+    lib.dwf_set_option.argtypes = [vp, i, d]
+    lib.dwf_measure_peak.argtypes = [i, vp, ctypes.POINTER(d)]
     for name in ("dwf_create", "dwf_update_links", "dwf_apply", "dwf_cg", "dwf_mspcg",
                  "dwf_force", "dwf_action", "dwf_batch_solve", "dwf_profile_enable",
-                 "dwf_profile_read", "dwf_mdagm_noalloc"):
+                 "dwf_profile_read", "dwf_mdagm_noalloc", "dwf_set_option",
+                 "dwf_measure_peak"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -182,13 +192,19 @@ def dwf_apply(h: Handle, op, inp, out, prec="f64"):
     return out
 
 
-def dwf_cg(h: Handle, phi, x, tol, maxit, prec="f64", history: int = 0, raise_on_fail=True):
+def dwf_cg(h: Handle, phi, x, tol, maxit, prec="f64", history: int = 0, raise_on_fail=True,
+           curvature: bool = False):
+    """history: record up to this many relative residual norms; curvature: also record
+    <p_k, A p_k> / ||phi||^2 per iteration (the Lanczos coefficients of FP64 CG)."""
     st = Stats()
-    buf = None
+    buf = cbuf = None
     if history:
         buf = (ctypes.c_double * history)()
         st.history = buf
         st.history_capacity = history
+        if curvature:
+            cbuf = (ctypes.c_double * history)()
+            st.curvature_history = cbuf
     s = load().dwf_cg(h.ptr, _ptr(phi), _ptr(x), float(tol), int(maxit), _prec(prec),
                       ctypes.byref(st))
     _check(s, () if raise_on_fail else (DWF_ERR_NOT_CONVERGED,))
@@ -269,3 +285,16 @@ def dwf_mdagm_noalloc(dims, Ls, M5, mf, b, c, links, inp, out, prec="f64", strea
                                     _ptr(links), _ptr(inp), _ptr(out), _prec(prec),
                                     _stream_ptr(stream)))
     return out
+
+
+def dwf_set_option(h: Handle, option: int, value: float):
+    """Per-handle option: OPT_WAIT_LIMIT_US (bounded device waits) or OPT_TEST_WAIT_PROBE."""
+    _check(load().dwf_set_option(h.ptr, int(option), float(value)))
+
+
+def dwf_measure_peak(which: str = "f64", stream=None) -> float:
+    """Measured FMA peak of the current device in TFLOP/s ("f64": DFMA, "f32": FFMA)."""
+    t = ctypes.c_double()
+    _check(load().dwf_measure_peak({"f64": 0, "f32": 1}[which], _stream_ptr(stream),
+                                   ctypes.byref(t)))
+    return t.value

@@ -52,10 +52,30 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
     called = []
-    monkeypatch.setattr(bench, "oracle_sample", lambda *a, **k: called.append(1))
+    monkeypatch.setattr(bench, "cpu_model", lambda *a, **k: called.append(1))
+    import oracle.dwf_oracle as o
+    monkeypatch.setattr(o, "mdagm", lambda *a, **k: called.append(1))
     bench.run_reference(bench.argparse.Namespace(gpus=2, steps=1, warmup=0, local_op="exact",
-                                                 l=1))
+                                                 l=6))
     assert not called and capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_0(monkeypatch, capsys):
+    """Rank 0 times the oracle's A on the sample lattice (stubbed here by a fixed cost) and
+    prints one JSON line with the reference fields."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle.dwf_oracle as o
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr(o, "mdagm", lambda *a, **k: None)
+    bench.run_reference(bench.argparse.Namespace(gpus=1, steps=2, warmup=1, local_op="exact",
+                                                 l=6))
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["higher_is_better"] is False
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["value"] >= 0
 
 
 def test_single_rank_max_is_identity():

@@ -237,3 +237,87 @@ def test_zero_source_gives_zero_solution(solver):
         st = dwf.dwf_cg(h, z, x, 1e-10, 100, solver[3:])
     assert st["iterations"] == 0
     assert np.count_nonzero(host(x)) == 0
+
+
+# ---------------------------------------------------------------------------------------
+# The exact block operator P_s A P_s at block shapes that span several 32-site tiles and have
+# interior sites: 6^4 blocks (648 even sites = 21 tiles, the benchmark workload's block
+# shape) and 8^4 blocks.  FP64 MSPCG must follow the oracle step by step; the comparison runs
+# a fixed number of outer iterations (maxit) so the oracle finishes in seconds.
+# ---------------------------------------------------------------------------------------
+MULTI_TILE = {
+    # name: dims, Ls, block, (b, c), mf, local iterations l, outer iterations, seed
+    "shamir_12x12x6x6_ls4_b6": ((12, 12, 6, 6), 4, (6, 6, 6, 6), (1.0, 0.0), 0.1, 2, 6, 31),
+    "mobius_12x6x6x6_ls8_b6": ((12, 6, 6, 6), 8, (6, 6, 6, 6), (1.5, 0.5), 0.05, 3, 6, 32),
+    "shamir_16x8x8x8_ls4_b8": ((16, 8, 8, 8), 4, (8, 8, 8, 8), (1.0, 0.0), 0.1, 2, 5, 33),
+}
+
+
+def multi_tile(name):
+    if name not in _cache:
+        dims, Ls, blk, (b, c), mf, l, n, seed = MULTI_TILE[name]
+        rng = np.random.default_rng(seed)
+        p = o.DWFParams(dims, Ls, 1.8, mf, b, c)
+        U = inputs.gauge_links(dims, 0.3, rng)
+        phi = inputs.even_source(dims, Ls, rng)
+        _cache[name] = (p, U, phi, blk, l, n)
+    return _cache[name]
+
+
+@pytest.mark.parametrize("name", sorted(MULTI_TILE))
+def test_mspcg_exact_multi_tile_blocks_follow_oracle(name):
+    dwf = lib()
+    p, U, phi, blk, l, n = multi_tile(name)
+    xo, ko, hist = o.mspcg(U, phi, p, blk, l, 1e-14, n, local_op="exact")
+    assert ko == n
+    h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
+    x = cuda(np.zeros_like(phi))
+    st = dwf.dwf_mspcg(h, blk, l, "f64", "f64", cuda(phi), x, 1e-14, n,
+                       local_op=dwf.LOCAL_EXACT, history=n + 4, raise_on_fail=False)
+    assert st["status"] == dwf.DWF_ERR_NOT_CONVERGED and st["iterations"] == n
+    for k in range(n):
+        assert abs(st["history"][k] - hist[k + 1]) <= 1e-6 * hist[k + 1], (k, st["history"][k],
+                                                                         hist[k + 1])
+    assert rel(host(x), xo) <= 1e-9
+
+
+@pytest.mark.parametrize("inner", ["f16", "bf16"])
+@pytest.mark.parametrize("name", ["shamir_12x12x6x6_ls4_b6", "mobius_12x6x6x6_ls8_b6"])
+def test_mspcg_mixed_multi_tile_blocks_true_residual(name, inner):
+    """16-bit local solves, FP32 outer CG, FP64 reliable updates on the multi-tile blocks:
+    the oracle recomputes the true residual of the returned solution."""
+    dwf = lib()
+    p, U, phi, blk, l, n = multi_tile(name)
+    h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
+    x = cuda(np.zeros_like(phi))
+    st = dwf.dwf_mspcg(h, blk, l, inner, "f32", cuda(phi), x, 1e-10, 5000,
+                       local_op=dwf.LOCAL_EXACT)
+    assert st["true_residual"] <= 1e-10
+    assert o.true_residual(U, host(x), phi, p) <= 1.5e-10
+
+
+def test_cg_lanczos_kappa_matches_dense_spectrum():
+    """The CG coefficients recorded by dwf_cg (residual norms and curvatures <p, A p>) give
+    the Lanczos tridiagonal of A; its extreme eigenvalues are those of the dense A built by
+    the oracle on a 2^4 x 4 lattice."""
+    import bench
+    dwf = lib()
+    dims, Ls = (2, 2, 2, 2), 4
+    rng = np.random.default_rng(61)
+    p = o.DWFParams(dims, Ls, 1.8, 0.2, 1.5, 0.5)
+    U = inputs.gauge_links(dims, 0.3, rng)
+    phi = inputs.even_source(dims, Ls, rng)
+    n = phi.size
+    A = np.zeros((n, n), complex)
+    for j in range(n):
+        e = np.zeros(n, complex)
+        e[j] = 1.0
+        A[:, j] = o.mdagm(U, e.reshape(phi.shape), p).reshape(-1)
+    ev = np.linalg.eigvalsh((A + A.conj().T) / 2)
+    h = dwf.dwf_create(dims, Ls, p.M5, p.mf, p.b, p.c, cuda(U))
+    x = cuda(np.zeros_like(phi))
+    st = dwf.dwf_cg(h, cuda(phi), x, 1e-13, 2000, "f64", history=2000, curvature=True)
+    kappa, lmin, lmax = bench.lanczos_kappa(st["history"], st["curvature_history"])
+    assert abs(lmax - ev[-1]) <= 1e-8 * ev[-1]
+    assert abs(lmin - ev[0]) <= 1e-4 * ev[0]
+    assert abs(kappa - ev[-1] / ev[0]) <= 1e-4 * kappa

@@ -365,7 +365,7 @@ def test_blocked_operator_is_block_diagonal():
 
 
 def test_block_local_operator_vs_exact_block():
-    """P_s A P_s (the paper's 'same diagonal blocks as A', Eq. 5) and the dropped-hop block
+    """P_s A P_s (the block-diagonal part of A, Eq. 5) and the dropped-hop block
     operator differ only on sites next to a block face (the second-neighbour terms of D^dag D,
     Sec. 2.2); both are Hermitian positive definite (Sec. 2.3)."""
     rng = np.random.default_rng(13)
