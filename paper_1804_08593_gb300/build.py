@@ -40,11 +40,15 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list | None = N
     """Compiles every csrc/*.cu and links lib/libdwf.so; returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    # stage_ls.cu is compiled once per (storage precision, Ls, dag): its kernel variants dominate
-    # the build, and the split lets them compile in parallel
+    # stage_ls.cu is compiled once per (storage precision, Ls, dag) and local_p.cu once per
+    # storage precision: their kernel variants dominate the build, and the split lets them
+    # compile in parallel
     units = []
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
-        if os.path.basename(src) == "stage_ls.cu":
+        if os.path.basename(src) == "local_p.cu":
+            for p in STAGE_PRECS:
+                units.append((src, [f"-DDWF_LOCAL_P={p}"], f"local_p{p}.o"))
+        elif os.path.basename(src) == "stage_ls.cu":
             for p in STAGE_PRECS:
                 for ls in STAGE_LS:
                     for dag in (0, 1):

@@ -467,4 +467,32 @@ struct BatchSeg {
   int ntiles;
 };
 
+// Writes the 9 complex elements v[k] = (re, im) of one link as 16-byte chunks.
+template <int P>
+__device__ __forceinline__ void store_link9(void* out, long Vp, long idx, int d,
+                                            const double (&re)[9], const double (&im)[9]) {
+  constexpr int NCHL = Prec<P>::NCHL;
+  uint4* o = reinterpret_cast<uint4*>(out) + (long)d * NCHL * Vp + idx;
+  if constexpr (P == P64) {
+    for (int k = 0; k < 9; k++) *reinterpret_cast<double2*>(o + k * Vp) = make_double2(re[k], im[k]);
+  } else if constexpr (P == P32) {
+    for (int k = 0; k < 5; k++) {
+      const int a = 2 * k, b = 2 * k + 1;
+      *reinterpret_cast<float4*>(o + k * Vp) =
+          make_float4((float)re[a], (float)im[a], b < 9 ? (float)re[b] : 0.f,
+                      b < 9 ? (float)im[b] : 0.f);
+    }
+  } else {
+    constexpr bool BF = (P == PB16);
+    for (int k = 0; k < 3; k++) {
+      uint32_t w[4];
+      for (int j = 0; j < 4; j++) {
+        const int e = 4 * k + j;
+        w[j] = e < 9 ? f2h((float)re[e], (float)im[e], BF) : 0u;
+      }
+      o[k * Vp] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 }  // namespace dwf

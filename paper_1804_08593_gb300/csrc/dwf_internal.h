@@ -66,8 +66,37 @@ struct Halo {
   ~Halo();
 };
 
+struct SimdArgs;
+
+// Block-SIMD geometry of the local solves for one block shape and one local operator (see
+// local_kernel.cuh): the block-relative positions of E = BE ++ HE and O = BO ++ HO, their
+// neighbour tables, per-phase schedules, element <-> outer-site maps and packed links.
+struct SimdLocal {
+  bool exact = false;
+  int nb = 0, NB = 0, ngroups = 0;
+  int nBE = 0, nE = 0, nO = 0;
+  long sB = 0, sE = 0, sO = 0;
+  uint32_t* nbrE = nullptr;   // [nE][8] -> O position or SIMD_ABSENT
+  uint32_t* nbrO = nullptr;   // [nO][8] -> E position or SIMD_ABSENT
+  int* sch = nullptr;         // P1 (nO) | P2 (nE) | P3 (nO) | P4 (nBE) schedules
+  int nsch[4] = {0, 0, 0, 0};
+  long sch_off[4] = {0, 0, 0, 0};
+  int* lexE = nullptr;        // [sE] element -> lexicographic site (-1: none)
+  int* lexO = nullptr;        // [sO]
+  int* fwd = nullptr;         // [sB] BE element -> whole-lattice even index (-1: none)
+  int* inv = nullptr;         // [V/2 rounded to 32] whole-lattice even index -> BE element
+  void* linksE[4] = {};
+  void* linksO[4] = {};
+  bool links_valid[4] = {false, false, false, false};
+  unsigned* ctr = nullptr;    // barrier counters
+  double* partial = nullptr;
+  int cap_slots = 0, cap_C = 0;
+  ~SimdLocal();
+};
+
 // Device tables and packed links of one site ordering.
 struct Layout {
+  std::unique_ptr<SimdLocal> simd[2];      // [exact]: local solves in the block-SIMD layout
   std::unique_ptr<Halo> halo;              // built on demand (exact block operator)
   Geom g;
   uint32_t* nbr[2] = {nullptr, nullptr};   // [8][Vp] per output parity
@@ -224,6 +253,21 @@ template <int P, int LS, bool DAG>
 cudaError_t stage_dispatch_ls(const StageArgs& a, bool blocked, cudaStream_t st);
 cudaError_t launch_stage_prec(int prec, const StageArgs& a, int Ls, bool dag, bool blocked,
                               cudaStream_t st);
+
+// ---- block-SIMD local solves (local_solve.cu, local_p.cu) ----
+dwf_status ensure_simd(dwf_ctx* h, Layout* lay, bool exact, SimdLocal** out);
+// Runs the l local CG iterations of every block from a zero guess on r_local = f r_outer,
+// f = sqrt(num / *den) (num when den is null); the solution is left in the BE field `x`
+// (element layout; S->inv maps whole-lattice even sites to elements).  One cooperative launch.
+struct SimdFields {
+  void *x, *p, *u, *r, *t, *y;
+};
+dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const void* r_outer,
+                            int prec_outer, long Vp_outer, double num, const double* den,
+                            const SimdFields& F);
+template <int P>
+cudaError_t simd_launch_p(const SimdArgs& a, int Ls, int* grid_cap, int nsm, cudaStream_t st,
+                          bool query);
 
 // ---- vector kernels (blas.cu) ----
 struct VecArgs {

@@ -1,0 +1,595 @@
+// The multisplitting preconditioner's local solves (Sec. 2.3, Eqs. 4-5) in one persistent,
+// cooperative kernel: l iterations of plain CG on A_s x_s = r_s for every lattice block s at
+// once, zero initial guess, block-local dot products.
+//
+// Block-SIMD layout.  All blocks have the same shape, so the sites a block's operator touches
+// are the same set of block-relative positions for every block: BE/BO (the block's even/odd
+// sites), and for A_s = P_s A P_s also HO (odd sites one hop outside, where D_oe of a
+// block-supported vector lives) and HE (even sites outside reached from BO or HO, where Mpc of
+// a block-supported vector lives).  E = BE ++ HE and O = BO ++ HO are stored position-major:
+// element e = position * NB + block, so the 32 lanes of a warp are 32 blocks at one position.
+// Every lane then has the same neighbour pattern (one broadcast table entry per direction, no
+// divergence, hops that are absent at that position skipped as a whole), and every neighbour
+// load is 32 consecutive elements of a 16-byte chunk (512 contiguous bytes).  Each block owns
+// its halo positions, so blocks never exchange data: the local solves need no communication,
+// as in the paper.
+//
+// Work split.  Blocks come in groups of 32 (one lane each); a fixed set of C CTAs (a "slot")
+// runs every phase of every iteration of its block groups, each CTA taking positions from a
+// cost-sorted schedule in round robin.  Phases of one CG iteration on A_s = Mpc_s^dag Mpc_s:
+//   P1  t = [D+ M5op^-1] Dh_oe (D+ p)        on O  (input on BE)
+//   P2  y = M5op p - 1/4 Dh_eo t             on E, per-block ||y||^2 = <p, A_s p> -> alpha
+//   P3  s = [M5op^-dag D+^dag] Dh_oe^dag y   on O
+//   P4  r -= alpha (M5op^dag y - 1/4 D+^dag Dh_eo^dag s)  on BE, per-block ||r||^2 -> beta
+//   P5  x += alpha p, p = r + beta p, u = D+ p            on BE
+// separated by barriers among the slot's CTAs only (a counter in global memory; every wait
+// is bounded in time and reports an error instead of hanging).  The per-block reductions are
+// one FP64 partial per (CTA, block), summed in a fixed order by every CTA after the barrier
+// (deterministic, and every CTA holds the same alpha and beta).  The launch is cooperative, so
+// all CTAs are resident at once.
+#pragma once
+
+#include "dwf_device.cuh"
+#include "tc_m5.cuh"
+
+namespace dwf {
+
+constexpr uint32_t SIMD_ABSENT = 0xffffffffu;
+
+struct SimdArgs {
+  int NB, nb, nBE, nE, nO;       // block stride, blocks, positions of BE / E / O
+  int ngroups, C, nslots;        // 32-block groups, CTAs per slot, slots
+  long sB, sE, sO;               // element strides of BE, E and O fields (positions * NB)
+  const uint32_t* nbrE;          // [nE][8]: neighbour position in O, or SIMD_ABSENT
+  const uint32_t* nbrO;          // [nO][8]: neighbour position in E, or SIMD_ABSENT
+  const int* sch[4];             // cost-sorted positions of P1 (O), P2 (E), P3 (O), P4 (BE)
+  int nsch[4];
+  const void* linksE;            // [8][NCHL][sE] links of the E sites (backward ones daggered)
+  const void* linksO;            // [8][NCHL][sO]
+  const int* fwd;                // [sB]: BE element -> site of the outer field (-1: none)
+  void *x, *p, *u, *r;           // BE fields
+  void* t;                       // O field (t, then s)
+  void* y;                       // E field
+  const void* r_outer;           // residual of the outer iteration, [s][chunk][Vp_outer]
+  int prec_outer;
+  long Vp_outer;
+  double num;                    // r_local = f r_outer, f = sqrt(num / *den) or num (den null)
+  const double* den;
+  Coef5<double> k64;             // M5op = la + lb K, D+ = db + dc K, recurrence r, inva, kappa,
+  Coef5<float> k32;              // pre = b when D+ = b (absorbed pre-op), else 1
+  double hs_b;                   // hop scale of the last stage: -1/4, or -b/4 when D+ = b
+  int trivial;                   // c == 0: D+ = b, no pre-op field u
+  int l;                         // local iterations
+  unsigned* ctr;                 // [nslots] barrier counters, zero at launch
+  double* partial;               // [nslots][C][32] per-CTA, per-block partial sums
+  unsigned long long wait_ns;
+  int* err;
+};
+
+template <typename A>
+__device__ __forceinline__ Coef5<A> simd_coef(const SimdArgs& a) {
+  if constexpr (sizeof(A) == 8) return a.k64; else return a.k32;
+}
+
+// Spinor of element e, slice s, from a field written earlier in this kernel (loads through
+// L2: another SM may have written it since this SM last cached the line).
+template <int P>
+__device__ __forceinline__ void ld_spinor(Spinor<typename Prec<P>::acc>& out, const void* base,
+                                          long stride, long e, int s) {
+  constexpr int NCH = Prec<P>::NCH;
+  const uint4* q = reinterpret_cast<const uint4*>(base) + ((long)s * NCH) * stride + e;
+  if constexpr (P == P64) {
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const double2 v = __ldcg(reinterpret_cast<const double2*>(q + k * stride));
+      out.c[k] = {v.x, v.y};
+    }
+  } else if constexpr (P == P32) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(q + k * stride));
+      out.c[2 * k] = {v.x, v.y};
+      out.c[2 * k + 1] = {v.z, v.w};
+    }
+  } else {
+    constexpr bool BF = (P == PB16);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint4 v = __ldcg(q + k * stride);
+      const float2 a = h2f(v.x, BF), b = h2f(v.y, BF), c = h2f(v.z, BF), d = h2f(v.w, BF);
+      out.c[4 * k] = {a.x, a.y};
+      out.c[4 * k + 1] = {b.x, b.y};
+      out.c[4 * k + 2] = {c.x, c.y};
+      out.c[4 * k + 3] = {d.x, d.y};
+    }
+  }
+}
+
+// The tile's links of the live directions into shared memory, converted to the accumulation
+// type once for all slices: lk[(d * 9 + k) * 32 + lane].
+template <int P>
+__device__ __forceinline__ void simd_stage_links(cx<typename Prec<P>::acc>* lk, const void* links,
+                                                 long stride, long e0, uint32_t live, int tid,
+                                                 int nt) {
+  using A = typename Prec<P>::acc;
+  constexpr int NCHL = Prec<P>::NCHL;
+  const uint4* L = reinterpret_cast<const uint4*>(links);
+  for (int i = tid; i < 8 * NCHL * 32; i += nt) {
+    const int d = i / (NCHL * 32);
+    if (!((live >> d) & 1u)) continue;
+    const int ch = (i >> 5) % NCHL, ln = i & 31;
+    const uint4 v = __ldg(L + (long)(d * NCHL + ch) * stride + e0 + ln);
+    cx<A>* o = lk + (d * 9) * 32 + ln;
+    if constexpr (P == P64) {
+      const double2 w = *reinterpret_cast<const double2*>(&v);
+      o[ch * 32] = {w.x, w.y};
+    } else if constexpr (P == P32) {
+      const float4 w = *reinterpret_cast<const float4*>(&v);
+      o[(2 * ch) * 32] = {w.x, w.y};
+      if (2 * ch + 1 < 9) o[(2 * ch + 1) * 32] = {w.z, w.w};
+    } else {
+      constexpr bool BF = (P == PB16);
+      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int k = 4 * ch + j;
+        if (k < 9) {
+          const float2 f = h2f(wv[j], BF);
+          o[k * 32] = {f.x, f.y};
+        }
+      }
+    }
+  }
+}
+
+// acc += sum over live directions d of the hop from element nb[d] * NB + eg of `in`.
+template <int P, bool DAG>
+__device__ __forceinline__ void simd_hop(Spinor<typename Prec<P>::acc>& acc,
+                                         const uint32_t (&nb)[8], uint32_t live, const void* in,
+                                         long stride, int NB, long eg, int s,
+                                         const cx<typename Prec<P>::acc>* lk, int lane) {
+  using A = typename Prec<P>::acc;
+#pragma unroll
+  for (int d = 0; d < 8; d++) {
+    if (!((live >> d) & 1u)) continue;
+    Spinor<A> psi;
+    ld_spinor<P>(psi, in, stride, (long)nb[d] * NB + eg, s);
+    cx<A> u[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) u[k] = lk[(d * 9 + k) * 32 + lane];
+    // forward hop (1 - gamma_mu), backward (1 + gamma_mu); the adjoint swaps them
+    const A sgn = (((d & 1) != 0) != DAG) ? A(1) : A(-1);
+    switch (d >> 1) {
+      case 0: hop_term_u<P, 0>(acc, psi, u, sgn); break;
+      case 1: hop_term_u<P, 1>(acc, psi, u, sgn); break;
+      case 2: hop_term_u<P, 2>(acc, psi, u, sgn); break;
+      default: hop_term_u<P, 3>(acc, psi, u, sgn); break;
+    }
+  }
+}
+
+// buf[s][24][32] <-> the per-thread spinor of slice s
+template <typename A>
+__device__ __forceinline__ void to_buf(A* buf, const Spinor<A>& v, int s, int lane) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    buf[(s * 24 + 2 * k) * 32 + lane] = v.c[k].x;
+    buf[(s * 24 + 2 * k + 1) * 32 + lane] = v.c[k].y;
+  }
+}
+template <typename A>
+__device__ __forceinline__ void from_buf(Spinor<A>& v, const A* buf, int s, int lane) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    v.c[k].x = buf[(s * 24 + 2 * k) * 32 + lane];
+    v.c[k].y = buf[(s * 24 + 2 * k + 1) * 32 + lane];
+  }
+}
+
+// Fifth-dimension post on the CTA's 32 x 24 columns in buf: D+ M5op^-1 (DAG false, times the
+// absorbed pre-op factor) or M5op^-dag D+^dag (DAG true).  Per chirality K is a cyclic shift
+// with a -mf corner, so M5op = la (1 + r S) is inverted by a one-sided recurrence plus the
+// Sherman-Morrison correction for the corner, kappa = r mf / (1 + mf (-r)^Ls).
+template <typename A, int LS, bool DAG>
+__device__ __forceinline__ void post_recurrence(A* buf, const Coef5<A>& C, int tid, int nt) {
+  const A r = C.r, inva = C.inva, kappa = C.kappa;
+  const A b_ = C.db, c_ = C.dc, mfA = C.mf, pre = C.pre;
+  for (int col = tid; col < 24 * 32; col += nt) {
+    const int c = col >> 5, l = col & 31;
+    const bool lower = ((c < 12) != DAG);
+    A v[LS];
+#pragma unroll
+    for (int t = 0; t < LS; t++) v[t] = buf[(t * 24 + c) * 32 + l];
+    if (DAG) {   // D+^dag first
+      A w[LS];
+#pragma unroll
+      for (int t = 0; t < LS; t++) {
+        const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
+                           : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
+        w[t] = b_ * v[t] + c_ * nb;
+      }
+#pragma unroll
+      for (int t = 0; t < LS; t++) v[t] = w[t];
+    }
+    if (lower) {
+#pragma unroll
+      for (int t = 1; t < LS; t++) v[t] = v[t] - r * v[t - 1];
+      const A e = kappa * v[LS - 1];
+      A g = A(1);
+#pragma unroll
+      for (int t = 0; t < LS; t++) {
+        v[t] = (v[t] + e * g) * inva;
+        g *= -r;
+      }
+    } else {
+#pragma unroll
+      for (int t = LS - 2; t >= 0; t--) v[t] = v[t] - r * v[t + 1];
+      const A e = kappa * v[0];
+      A g = A(1);
+#pragma unroll
+      for (int t = LS - 1; t >= 0; t--) {
+        v[t] = (v[t] + e * g) * inva;
+        g *= -r;
+      }
+    }
+    if (!DAG) {   // then D+ (times the absorbed pre-op factor)
+      A w[LS];
+#pragma unroll
+      for (int t = 0; t < LS; t++) {
+        const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
+                           : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
+        w[t] = pre * (b_ * v[t] + c_ * nb);
+      }
+#pragma unroll
+      for (int t = 0; t < LS; t++) v[t] = w[t];
+    }
+#pragma unroll
+    for (int t = 0; t < LS; t++) buf[(t * 24 + c) * 32 + l] = v[t];
+  }
+}
+
+// v <- D+ v (P+ spins from s-1, P- spins from s+1, -mf at the walls), or D+^dag v (P+ from
+// s+1, P- from s-1), through the slices' copies in buf (which this call fills).
+template <typename A, int LS, bool DAG>
+__device__ __forceinline__ void dplus_slices(Spinor<A>& v, A* buf, const Coef5<A>& C, int s,
+                                             int lane) {
+  to_buf(buf, v, s, lane);
+  __syncthreads();
+  const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
+  const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    const bool plus = k < 6;
+    const bool from_up = DAG ? plus : !plus;
+    const int sn = from_up ? su : sd;
+    const A f = from_up ? fu : fd;
+    v.c[k].x = C.db * v.c[k].x + C.dc * f * buf[(sn * 24 + 2 * k) * 32 + lane];
+    v.c[k].y = C.db * v.c[k].y + C.dc * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+  }
+  __syncthreads();
+}
+
+// acc += M5op x (DAG false) or M5op^dag x (DAG true) at slice s: la x_s + lb (K or K^dag) x.
+template <int P, bool DAG>
+__device__ __forceinline__ void add_m5(Spinor<typename Prec<P>::acc>& acc, const void* x,
+                                       long stride, long e, int s, int ls,
+                                       const Coef5<typename Prec<P>::acc>& C) {
+  using A = typename Prec<P>::acc;
+  Spinor<A> x0, xu, xd;
+  ld_spinor<P>(x0, x, stride, e, s);
+  ld_spinor<P>(xu, x, stride, e, s + 1 < ls ? s + 1 : 0);
+  ld_spinor<P>(xd, x, stride, e, s > 0 ? s - 1 : ls - 1);
+  const A fu = (s + 1 < ls) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    const bool plus = k < 6;
+    const bool from_up = DAG ? plus : !plus;
+    const cx<A> nb = from_up ? cscale(fu, xu.c[k]) : cscale(fd, xd.c[k]);
+    acc.c[k].x += C.la * x0.c[k].x + C.lb * nb.x;
+    acc.c[k].y += C.la * x0.c[k].y + C.lb * nb.y;
+  }
+}
+
+template <typename A>
+__device__ __forceinline__ A norm2(const Spinor<A>& v) {
+  A n = A(0);
+#pragma unroll
+  for (int k = 0; k < 12; k++) n = fma(v.c[k].x, v.c[k].x, fma(v.c[k].y, v.c[k].y, n));
+  return n;
+}
+
+// Barrier of the C CTAs of one slot: the counter counts arrivals; `target` is the number of
+// arrivals that completes this barrier.  Bounded: gives up after the wait limit, records the
+// error and returns false in every thread of the CTA (which then leaves the kernel; the
+// others then give up at their next barrier, so the launch always ends).
+__device__ __forceinline__ bool slot_barrier(unsigned* ctr, unsigned target,
+                                             unsigned long long wait_ns, int* err) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    int ok = 1;
+    const unsigned long long lim = wait_ns ? wait_ns : tc::DEFAULT_WAIT_NS;
+    const unsigned long long t0 = tc::globaltimer_ns();
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+      if (v >= target) break;
+      if (tc::globaltimer_ns() - t0 > lim) {
+        ok = 0;
+        if (err) atomicExch(err, 1);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// One FP64 partial per (CTA, lane) of the thread-level values v (summed over the slices).
+template <typename A, int LS>
+__device__ __forceinline__ void write_partial(A v, A (*red)[32], double* dst, int s, int lane) {
+  red[s][lane] = v;
+  __syncthreads();
+  if (s == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < LS; w++) t += (double)red[w][lane];
+    dst[lane] = t;
+  }
+}
+
+// Sum over the slot's C partials of this lane's block (fixed order); valid in every thread.
+__device__ __forceinline__ double slot_total(const double* part, int C, double* sc, int s,
+                                             int lane) {
+  if (s == 0) {
+    double t = 0.0;
+    for (int c = 0; c < C; c++) t += __ldcg(part + c * 32 + lane);
+    sc[lane] = t;
+  }
+  __syncthreads();
+  const double t = sc[lane];
+  __syncthreads();
+  return t;
+}
+
+template <int P, int LS>
+__global__ void __launch_bounds__(32 * LS, (P == P64) ? 1 : 2)
+simd_local_kernel(const SimdArgs a) {
+  using A = typename Prec<P>::acc;
+  extern __shared__ __align__(16) unsigned char smem[];
+  cx<A>* lk = reinterpret_cast<cx<A>*>(smem);                    // [8][9][32]
+  A* buf = reinterpret_cast<A*>(smem + 8 * 9 * 32 * sizeof(cx<A>));   // [LS][24][32]
+  __shared__ A red[LS][32];
+  __shared__ double sc[32];
+  constexpr int NT = 32 * LS;
+  const int lane = threadIdx.x, s = threadIdx.y, tid = lane + 32 * s;
+  const int C = a.C, slot = blockIdx.x / C, ci = blockIdx.x % C;
+  if (slot >= a.nslots) return;
+  unsigned* ctr = a.ctr + slot;
+  double* part = a.partial + (long)slot * C * 32;
+  unsigned nbar = 0;
+  const Coef5<A> K = simd_coef<A>(a);
+  const int NB = a.NB;
+  const long sB = a.sB, sE = a.sE, sO = a.sO;
+  const void* pin1 = a.trivial ? a.p : a.u;   // input of P1: D+ p (p itself when D+ = b)
+  auto barrier = [&]() -> bool {
+    ++nbar;
+    return slot_barrier(ctr, nbar * (unsigned)C, a.wait_ns, a.err);
+  };
+
+  for (int g = slot; g < a.ngroups; g += a.nslots) {
+    const long eg = (long)g * 32 + lane;   // this lane's block, as an element offset
+    double rho, alpha = 0.0, beta = 0.0;
+    // ---- P0: r = f r_outer (gathered into the block layout), p = r, x = 0, u = D+ p
+    {
+      double f = a.num;
+      if (a.den) f = sqrt(a.num / *a.den);
+      A nrm = A(0);
+      for (int pos = ci; pos < a.nBE; pos += C) {
+        const long e = (long)pos * NB + eg;
+        const int o = __ldg(a.fwd + e);
+        Spinor<A> v;
+        if (o < 0) {
+          zero(v);
+        } else if (a.prec_outer == P64) {
+          Spinor<double> w;
+          load_spinor<P64>(w, a.r_outer, a.Vp_outer, o, s);
+#pragma unroll
+          for (int k = 0; k < 12; k++) v.c[k] = {A(w.c[k].x * f), A(w.c[k].y * f)};
+        } else {
+          Spinor<float> w;
+          load_spinor<P32>(w, a.r_outer, a.Vp_outer, o, s);
+          const A ff = A(f);
+#pragma unroll
+          for (int k = 0; k < 12; k++) v.c[k] = {A(w.c[k].x) * ff, A(w.c[k].y) * ff};
+        }
+        store_spinor<P>(a.r, sB, e, s, v);
+        store_spinor<P>(a.p, sB, e, s, v);
+        Spinor<A> zz;
+        zero(zz);
+        store_spinor<P>(a.x, sB, e, s, zz);
+        Spinor<A> back = v;
+        round_to_storage<P>(back);
+        nrm += norm2(back);
+        if (!a.trivial) {
+          dplus_slices<A, LS, false>(back, buf, K, s, lane);
+          store_spinor<P>(a.u, sB, e, s, back);
+        }
+      }
+      write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
+      if (!barrier()) return;
+      rho = slot_total(part, C, sc, s, lane);
+    }
+    for (int k = 0; k < a.l; k++) {
+      const bool last = (k + 1 == a.l);
+      // ---- P1: t = [D+ M5op^-1] Dh_oe (D+ p) on O
+      for (int i = ci; i < a.nsch[0]; i += C) {
+        const int pos = __ldg(a.sch[0] + i);
+        uint32_t nb[8], live = 0;
+#pragma unroll
+        for (int d = 0; d < 8; d++) {
+          nb[d] = __ldg(a.nbrO + pos * 8 + d);
+          if (nb[d] != SIMD_ABSENT && nb[d] < (uint32_t)a.nBE) live |= 1u << d;
+        }
+        simd_stage_links<P>(lk, a.linksO, sO, (long)pos * NB + (long)g * 32, live, tid, NT);
+        __syncthreads();
+        Spinor<A> acc;
+        zero(acc);
+        simd_hop<P, false>(acc, nb, live, pin1, sB, NB, eg, s, lk, lane);
+        to_buf(buf, acc, s, lane);
+        __syncthreads();
+        post_recurrence<A, LS, false>(buf, K, tid, NT);
+        __syncthreads();
+        from_buf(acc, buf, s, lane);
+        store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
+        __syncthreads();
+      }
+      if (!barrier()) return;
+      // ---- P2: y = M5op p - 1/4 Dh_eo t on E; <p, A_s p> = ||y||^2 over the block
+      {
+        A nrm = A(0);
+        const A hs = A(-0.25);
+        for (int i = ci; i < a.nsch[1]; i += C) {
+          const int pos = __ldg(a.sch[1] + i);
+          uint32_t nb[8], live = 0;
+#pragma unroll
+          for (int d = 0; d < 8; d++) {
+            nb[d] = __ldg(a.nbrE + pos * 8 + d);
+            if (nb[d] != SIMD_ABSENT) live |= 1u << d;
+          }
+          simd_stage_links<P>(lk, a.linksE, sE, (long)pos * NB + (long)g * 32, live, tid, NT);
+          __syncthreads();
+          Spinor<A> acc;
+          zero(acc);
+          simd_hop<P, false>(acc, nb, live, a.t, sO, NB, eg, s, lk, lane);
+#pragma unroll
+          for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
+          const long e = (long)pos * NB + eg;
+          if (pos < a.nBE) add_m5<P, false>(acc, a.p, sB, e, s, LS, K);
+          nrm += norm2(acc);
+          if (!last) store_spinor<P>(a.y, sE, e, s, acc);
+          __syncthreads();
+        }
+        write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
+        if (!barrier()) return;
+        const double pap = slot_total(part, C, sc, s, lane);
+        alpha = (pap > 0.0 && isfinite(pap)) ? rho / pap : 0.0;
+      }
+      if (last) {
+        // ---- x += alpha p (the last iteration needs no new residual or direction)
+        const A al = A(alpha);
+        for (int pos = ci; pos < a.nBE; pos += C) {
+          const long e = (long)pos * NB + eg;
+          Spinor<A> xv, pv;
+          ld_spinor<P>(xv, a.x, sB, e, s);
+          ld_spinor<P>(pv, a.p, sB, e, s);
+#pragma unroll
+          for (int q = 0; q < 12; q++) {
+            xv.c[q].x += al * pv.c[q].x;
+            xv.c[q].y += al * pv.c[q].y;
+          }
+          store_spinor<P>(a.x, sB, e, s, xv);
+        }
+        break;
+      }
+      // ---- P3: s = [M5op^-dag D+^dag] Dh_oe^dag y on O
+      for (int i = ci; i < a.nsch[2]; i += C) {
+        const int pos = __ldg(a.sch[2] + i);
+        uint32_t nb[8], live = 0;
+#pragma unroll
+        for (int d = 0; d < 8; d++) {
+          nb[d] = __ldg(a.nbrO + pos * 8 + d);
+          if (nb[d] != SIMD_ABSENT) live |= 1u << d;
+        }
+        simd_stage_links<P>(lk, a.linksO, sO, (long)pos * NB + (long)g * 32, live, tid, NT);
+        __syncthreads();
+        Spinor<A> acc;
+        zero(acc);
+        simd_hop<P, true>(acc, nb, live, a.y, sE, NB, eg, s, lk, lane);
+        to_buf(buf, acc, s, lane);
+        __syncthreads();
+        post_recurrence<A, LS, true>(buf, K, tid, NT);
+        __syncthreads();
+        from_buf(acc, buf, s, lane);
+        store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
+        __syncthreads();
+      }
+      if (!barrier()) return;
+      // ---- P4: r -= alpha (M5op^dag y - 1/4 D+^dag Dh_eo^dag s) on BE; ||r||^2 -> beta
+      {
+        A nrm = A(0);
+        const A al = A(alpha), hs = A(a.hs_b);
+        for (int i = ci; i < a.nsch[3]; i += C) {
+          const int pos = __ldg(a.sch[3] + i);
+          uint32_t nb[8], live = 0;
+#pragma unroll
+          for (int d = 0; d < 8; d++) {
+            nb[d] = __ldg(a.nbrE + pos * 8 + d);
+            if (nb[d] != SIMD_ABSENT) live |= 1u << d;
+          }
+          simd_stage_links<P>(lk, a.linksE, sE, (long)pos * NB + (long)g * 32, live, tid, NT);
+          __syncthreads();
+          Spinor<A> acc;
+          zero(acc);
+          simd_hop<P, true>(acc, nb, live, a.t, sO, NB, eg, s, lk, lane);
+          if (!a.trivial) dplus_slices<A, LS, true>(acc, buf, K, s, lane);
+#pragma unroll
+          for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
+          const long e = (long)pos * NB + eg;
+          add_m5<P, true>(acc, a.y, sE, e, s, LS, K);
+          Spinor<A> rr;
+          ld_spinor<P>(rr, a.r, sB, e, s);
+#pragma unroll
+          for (int q = 0; q < 12; q++) {
+            rr.c[q].x -= al * acc.c[q].x;
+            rr.c[q].y -= al * acc.c[q].y;
+          }
+          store_spinor<P>(a.r, sB, e, s, rr);
+          round_to_storage<P>(rr);
+          nrm += norm2(rr);
+          __syncthreads();
+        }
+        write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
+        if (!barrier()) return;
+        const double rr_new = slot_total(part, C, sc, s, lane);
+        beta = (rho > 0.0 && isfinite(rr_new)) ? rr_new / rho : 0.0;
+        rho = rr_new;
+      }
+      // ---- P5: x += alpha p, p = r + beta p, u = D+ p on BE
+      {
+        const A al = A(alpha), be = A(beta);
+        for (int pos = ci; pos < a.nBE; pos += C) {
+          const long e = (long)pos * NB + eg;
+          Spinor<A> xv, pv, rv;
+          ld_spinor<P>(xv, a.x, sB, e, s);
+          ld_spinor<P>(pv, a.p, sB, e, s);
+          ld_spinor<P>(rv, a.r, sB, e, s);
+#pragma unroll
+          for (int q = 0; q < 12; q++) {
+            xv.c[q].x += al * pv.c[q].x;
+            xv.c[q].y += al * pv.c[q].y;
+            pv.c[q].x = rv.c[q].x + be * pv.c[q].x;
+            pv.c[q].y = rv.c[q].y + be * pv.c[q].y;
+          }
+          store_spinor<P>(a.x, sB, e, s, xv);
+          store_spinor<P>(a.p, sB, e, s, pv);
+          if (!a.trivial) {
+            round_to_storage<P>(pv);
+            dplus_slices<A, LS, false>(pv, buf, K, s, lane);
+            store_spinor<P>(a.u, sB, e, s, pv);
+          }
+        }
+      }
+      if (!barrier()) return;
+    }
+    // the slot's partial sums are reused by its next block group
+    if (g + a.nslots < a.ngroups && !barrier()) return;
+  }
+}
+
+}  // namespace dwf

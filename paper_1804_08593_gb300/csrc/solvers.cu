@@ -423,7 +423,20 @@ struct InnerVectors {
   void *ri, *xi, *pi, *ui, *ti, *yi, *si;
   bool exact = false;
   OpEngine::ExactBufs eb{};
+  SimdLocal* simd = nullptr;   // local solves in one persistent launch (else stage launches)
+  int prec = 0;                // storage precision of the local solves
 };
+
+// Which local solver MSPCG uses: the persistent block-SIMD kernel (default) or one launch per
+// operator stage (DWF_LOCAL_SOLVER=stages), kept as a second implementation to compare with.
+static bool use_simd_local() {
+  const char* e = getenv("DWF_LOCAL_SOLVER");
+  return !(e && strcmp(e, "stages") == 0);
+}
+
+static dwf_status precondition_stages(const OpEngine& Em, const OpEngine& Ei, const void* r,
+                                      const InnerVectors& iv, double* dsc, double* blk, int nb,
+                                      int l);
 
 // z = M^-1 r approximated by l local CG iterations per block from a zero guess (Eqs. 4-5),
 // with every block-local dot product reduced per block; then <r, z> (FR) or the
@@ -433,6 +446,56 @@ struct InnerVectors {
 static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const void* r, void* z,
                                const InnerVectors& iv, double* dsc, double* blk, int nb, int l,
                                bool flexible, const void* rold, ZSrc& zs) {
+  const int ip = iv.prec;
+  const bool scaled = (ip == P16 || ip == PB16);
+  const double nreal = 24.0 * Em.h->Ls * (double)(Em.g().V / 2);
+  // where the local solution lives: element order and stride, and its bytes
+  const int* zmap = nullptr;
+  long zvp = 0;
+  double zbytes = 0.0;
+  if (iv.simd) {
+    const SimdFields F{iv.xi, iv.pi, iv.ui, iv.ri, iv.ti, iv.yi};
+    DWF_TRY(simd_local_solve(Em.h, iv.simd, ip, l, r, Em.prec, Em.g().Vp,
+                             scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, F));
+    zmap = iv.simd->inv;
+    zvp = iv.simd->sB;
+    zbytes = (double)Em.h->Ls * (double)iv.simd->sB * 24.0 * (double)real_bytes(ip);
+  } else {
+    DWF_TRY(precondition_stages(Em, Ei, r, iv, dsc, blk, nb, l));
+    const bool remap = (Em.lay != Ei.lay);
+    zmap = remap ? Ei.lay->cb_inv : nullptr;
+    zvp = Ei.g().Vp;
+    zbytes = (double)field_bytes(Ei.g(), Ei.prec);
+  }
+  if (!flexible) {
+    RedArgs rz = Em.red(FIN_BETA, nullptr);
+    rz.rho = dsc + S_RHO;
+    rz.beta = dsc + S_BETA;
+    DWF_TRY(cast(Em, ip, iv.xi, nullptr, scaled ? nreal : 1.0,
+                 scaled ? dsc + S_RR : nullptr, 1, r, rz, nullptr, zmap, zvp));
+    zs.src = iv.xi;
+    zs.prec = ip;
+    zs.map = zmap;
+    zs.vp = zvp;
+    zs.num = scaled ? nreal : 1.0;
+    zs.den = scaled ? dsc + S_RR : nullptr;
+    zs.bytes = zbytes;
+  } else {
+    zs = ZSrc{};
+    DWF_TRY(cast(Em, ip, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
+                 r, Em.red(FIN_STORE, dsc + S_RZNEW), nullptr, zmap, zvp));
+    DWF_TRY(vop(Em, VOP_DOT, rold, z, Em.red(FIN_STORE, dsc + S_TMP)));
+    pr_beta_kernel<<<1, 1, 0, Em.h->stream>>>(dsc);
+    DWF_CUDA(cudaGetLastError());
+  }
+  return DWF_OK;
+}
+
+// The local solves as one launch per operator stage and CG update, block-local reductions as
+// CTA segments of the block-major site order; the solution is left in iv.xi.
+static dwf_status precondition_stages(const OpEngine& Em, const OpEngine& Ei, const void* r,
+                                      const InnerVectors& iv, double* dsc, double* blk, int nb,
+                                      int l) {
   const bool scaled = (Ei.prec == P16 || Ei.prec == PB16);
   const double nreal = 24.0 * Em.h->Ls * (double)(Em.g().V / 2);
   double* rho_b = blk;
@@ -487,29 +550,6 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
     }
     DWF_TRY(vec(Ei, va));
   }
-  if (!flexible) {
-    RedArgs rz = Em.red(FIN_BETA, nullptr);
-    rz.rho = dsc + S_RHO;
-    rz.beta = dsc + S_BETA;
-    DWF_TRY(cast(Em, Ei.prec, iv.xi, nullptr, scaled ? nreal : 1.0,
-                 scaled ? dsc + S_RR : nullptr, 1, r, rz, nullptr,
-                 remap ? Ei.lay->cb_inv : nullptr, Ei.g().Vp));
-    zs.src = iv.xi;
-    zs.prec = Ei.prec;
-    zs.map = remap ? Ei.lay->cb_inv : nullptr;
-    zs.vp = Ei.g().Vp;
-    zs.num = scaled ? nreal : 1.0;
-    zs.den = scaled ? dsc + S_RR : nullptr;
-    zs.bytes = (double)field_bytes(Ei.g(), Ei.prec);
-  } else {
-    zs = ZSrc{};
-    DWF_TRY(cast(Em, Ei.prec, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
-                 r, Em.red(FIN_STORE, dsc + S_RZNEW), nullptr,
-                 remap ? Ei.lay->cb_inv : nullptr, Ei.g().Vp));
-    DWF_TRY(vop(Em, VOP_DOT, rold, z, Em.red(FIN_STORE, dsc + S_TMP)));
-    pr_beta_kernel<<<1, 1, 0, Em.h->stream>>>(dsc);
-    DWF_CUDA(cudaGetLastError());
-  }
   return DWF_OK;
 }
 
@@ -522,8 +562,9 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   stats_init(stats);
   const Geom& g = layL->g;     // outer vectors
   const Geom& gb = lay->g;     // local solves
+  const bool simd = use_simd_local();
   long max_ctas = std::max(g.Vp, gb.Vp) / 32;
-  if (exact) {
+  if (exact && !simd) {
     // before the engines pack links: packing also gathers the halo copies
     DWF_TRY(ensure_halo(h, lay));
     max_ctas = std::max(max_ctas, lay->halo->He_tot / 32);
@@ -531,7 +572,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   OpEngine E64, Em, Ei;
   DWF_TRY(E64.init(h, layL, P64, false));
   DWF_TRY(Em.init(h, layL, middle, false));
-  DWF_TRY(Ei.init(h, lay, inner, true));
+  if (!simd) DWF_TRY(Ei.init(h, lay, inner, true));
   DWF_TRY(ensure_reduction(h, max_ctas * 2 + 64, gb.nblocks + 64));
   const size_t f64 = field_bytes(g, P64), fm = field_bytes(g, middle), fi = field_bytes(gb, inner);
   void *b64, *x64, *r64, *t1, *t2, *t3;
@@ -552,6 +593,18 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   DWF_TRY(h->ws->get("ms_zm", fm, &zm));
   if (flex) DWF_TRY(h->ws->get("ms_rold", fm, &rold));
   InnerVectors iv;
+  iv.prec = inner;
+  if (simd) {
+    DWF_TRY(ensure_simd(h, lay, exact, &iv.simd));
+    const size_t per = (size_t)h->Ls * 24 * real_bytes(inner);
+    DWF_TRY(h->ws->get("ms_ri", per * iv.simd->sB, &iv.ri));
+    DWF_TRY(h->ws->get("ms_xi", per * iv.simd->sB, &iv.xi));
+    DWF_TRY(h->ws->get("ms_pi", per * iv.simd->sB, &iv.pi));
+    DWF_TRY(h->ws->get("ms_ui", per * iv.simd->sB, &iv.ui));
+    DWF_TRY(h->ws->get("ms_ti", per * iv.simd->sO, &iv.ti));
+    DWF_TRY(h->ws->get("ms_yi", per * iv.simd->sE, &iv.yi));
+    iv.si = nullptr;
+  } else {
   DWF_TRY(h->ws->get("ms_ri", fi, &iv.ri));
   DWF_TRY(h->ws->get("ms_xi", fi, &iv.xi));
   DWF_TRY(h->ws->get("ms_pi", fi, &iv.pi));
@@ -569,6 +622,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
     DWF_TRY(h->ws->get("ms_th", per_site * H.Ho_tot, &iv.eb.t_halo));
     DWF_TRY(h->ws->get("ms_sh", per_site * H.Ho_tot, &iv.eb.s_halo));
     DWF_TRY(h->ws->get("ms_yh", per_site * H.He_tot, &iv.eb.y_halo));
+  }
   }
   double *dsc, *blk;
   DWF_TRY(h->ws->get("ms_scal", S_NSLOT * sizeof(double), (void**)&dsc));

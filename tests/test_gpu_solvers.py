@@ -112,7 +112,10 @@ def test_cg_failure_modes():
     assert np.all(host(z) == 0)
 
 
-def test_mspcg_fp64_matches_oracle():
+@pytest.mark.parametrize("solver", ["persistent", "stages"])
+def test_mspcg_fp64_matches_oracle(solver, monkeypatch):
+    if solver == "stages":
+        monkeypatch.setenv("DWF_LOCAL_SOLVER", "stages")
     dwf = lib()
     p, U, phi, xo, ko, hist = small_ms()
     h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
@@ -179,7 +182,10 @@ def exact_case():
     return _cache["ex"]
 
 
-def test_mspcg_exact_blocks_fp64_matches_oracle():
+@pytest.mark.parametrize("solver", ["persistent", "stages"])
+def test_mspcg_exact_blocks_fp64_matches_oracle(solver, monkeypatch):
+    if solver == "stages":
+        monkeypatch.setenv("DWF_LOCAL_SOLVER", "stages")
     dwf = lib()
     p, U, phi, xo, ko, hist = exact_case()
     h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
@@ -264,11 +270,23 @@ def multi_tile(name):
     return _cache[name]
 
 
+def multi_tile_oracle(name):
+    key = name + "/oracle"
+    if key not in _cache:
+        p, U, phi, blk, l, n = multi_tile(name)
+        _cache[key] = o.mspcg(U, phi, p, blk, l, 1e-14, n, local_op="exact")
+    return _cache[key]
+
+
+@pytest.mark.parametrize("solver", ["persistent", "stages"])
 @pytest.mark.parametrize("name", sorted(MULTI_TILE))
-def test_mspcg_exact_multi_tile_blocks_follow_oracle(name):
+def test_mspcg_exact_multi_tile_blocks_follow_oracle(name, solver, monkeypatch):
+    """Both local-solve implementations (one persistent launch; one launch per stage)."""
+    if solver == "stages":
+        monkeypatch.setenv("DWF_LOCAL_SOLVER", "stages")
     dwf = lib()
     p, U, phi, blk, l, n = multi_tile(name)
-    xo, ko, hist = o.mspcg(U, phi, p, blk, l, 1e-14, n, local_op="exact")
+    xo, ko, hist = multi_tile_oracle(name)
     assert ko == n
     h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
     x = cuda(np.zeros_like(phi))
