@@ -1,5 +1,6 @@
 // C ABI entry points: handle lifecycle, dwf_apply, error reporting, shared helpers.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -149,6 +150,12 @@ dwf_status dwf_create(dwf_t* handle, const int dims[4], int Ls, double M5, doubl
   h->c = c;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   h->device = dev;
+  // DWF_WAIT_LIMIT_US: initial limit of the handle's bounded device waits (profiler replays
+  // slow kernels down; the default is 10 ms)
+  if (const char* wl = getenv("DWF_WAIT_LIMIT_US")) {
+    const double us = atof(wl);
+    if (us >= 1.0 && us <= 1e7) h->wait_ns = (unsigned long long)(us * 1000.0);
+  }
   h->ws = std::make_unique<Workspace>();
   const long V = (long)dims[0] * dims[1] * dims[2] * dims[3];
   const size_t lbytes = (size_t)V * 4 * 9 * 16;

@@ -30,6 +30,7 @@
 #pragma once
 
 #include "dwf_device.cuh"
+#include "stage.cuh"
 #include "tc_m5.cuh"
 
 namespace dwf {
@@ -105,65 +106,150 @@ __device__ __forceinline__ void ld_spinor(Spinor<typename Prec<P>::acc>& out, co
   }
 }
 
-// The tile's links of the live directions into shared memory, converted to the accumulation
-// type once for all slices: lk[(d * 9 + k) * 32 + lane].
+// Shared memory of the local-solve kernel: two buffers of raw tile links ([8][NCHL][32] chunks
+// of 16 bytes; the next tile's links are copied in while the current tile computes), then one
+// region used first as the per-thread neighbour ring ([2][NCH][32 LS] chunks; not for FP64,
+// which loads neighbours directly) and then as the fifth-dimension buffer ([LS][24][32]).
 template <int P>
-__device__ __forceinline__ void simd_stage_links(cx<typename Prec<P>::acc>* lk, const void* links,
-                                                 long stride, long e0, uint32_t live, int tid,
-                                                 int nt) {
-  using A = typename Prec<P>::acc;
+__host__ __device__ constexpr size_t simd_lraw_bytes() {
+  return (size_t)8 * Prec<P>::NCHL * 32 * 16;
+}
+template <int P>
+__host__ __device__ constexpr bool simd_ring() { return P != P64; }
+template <int P>
+__host__ __device__ constexpr size_t simd_region_bytes(int ls) {
+  const size_t ring = simd_ring<P>() ? (size_t)2 * Prec<P>::NCH * 32 * ls * 16 : 0;
+  const size_t buf = (size_t)ls * 24 * 32 * sizeof(typename Prec<P>::acc);
+  return ring > buf ? ring : buf;
+}
+template <int P>
+__host__ __device__ constexpr size_t simd_smem_bytes(int ls) {
+  return 2 * simd_lraw_bytes<P>() + simd_region_bytes<P>(ls);
+}
+
+// Copies the links of the live directions of the tile at element e0 into lraw (cp.async
+// through L2; one commit group per thread).
+template <int P>
+__device__ __forceinline__ void simd_prefetch_links(uint4* lraw, const void* links, long stride,
+                                                    long e0, uint32_t live, int tid, int nt) {
   constexpr int NCHL = Prec<P>::NCHL;
   const uint4* L = reinterpret_cast<const uint4*>(links);
   for (int i = tid; i < 8 * NCHL * 32; i += nt) {
     const int d = i / (NCHL * 32);
     if (!((live >> d) & 1u)) continue;
     const int ch = (i >> 5) % NCHL, ln = i & 31;
-    const uint4 v = __ldg(L + (long)(d * NCHL + ch) * stride + e0 + ln);
-    cx<A>* o = lk + (d * 9) * 32 + ln;
-    if constexpr (P == P64) {
-      const double2 w = *reinterpret_cast<const double2*>(&v);
-      o[ch * 32] = {w.x, w.y};
-    } else if constexpr (P == P32) {
-      const float4 w = *reinterpret_cast<const float4*>(&v);
-      o[(2 * ch) * 32] = {w.x, w.y};
-      if (2 * ch + 1 < 9) o[(2 * ch + 1) * 32] = {w.z, w.w};
-    } else {
-      constexpr bool BF = (P == PB16);
-      const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+    cp_async16<false>(lraw + i, L + (long)(d * NCHL + ch) * stride + e0 + ln);
+  }
+  cp_async_commit();
+}
+
+// Live-hop mask of a table row: present entries (and, for be_only, entries < nBE).
+__device__ __forceinline__ uint32_t simd_live(const uint32_t* row, bool be_only, int nBE) {
+  uint32_t live = 0;
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        const int k = 4 * ch + j;
-        if (k < 9) {
-          const float2 f = h2f(wv[j], BF);
-          o[k * 32] = {f.x, f.y};
-        }
+  for (int d = 0; d < 8; d++) {
+    const uint32_t j = __ldg(row + d);
+    if (j != SIMD_ABSENT && (!be_only || j < (uint32_t)nBE)) live |= 1u << d;
+  }
+  return live;
+}
+
+template <int P, int MU, bool DAG, int D>
+__device__ __forceinline__ void simd_term(Spinor<typename Prec<P>::acc>& acc, const uint4* q,
+                                          int qs, const uint4* lraw, int lane) {
+  using A = typename Prec<P>::acc;
+  constexpr bool back = (D & 1) != 0;
+  const A sgn = (back != DAG) ? A(1) : A(-1);
+  if constexpr (P == P16 || P == PB16) {
+    const uint4 qq[3] = {q[0], q[qs], q[2 * qs]};
+    hop_term16<P, MU, true>(acc, qq, lraw + (D * 3) * 32 + lane, 32, sgn);
+  } else {
+    Spinor<A> psi;
+    if constexpr (P == P32) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        const float4 v = *reinterpret_cast<const float4*>(q + k * qs);
+        psi.c[2 * k] = {v.x, v.y};
+        psi.c[2 * k + 1] = {v.z, v.w};
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        const double2 v = *reinterpret_cast<const double2*>(q + k * qs);
+        psi.c[k] = {v.x, v.y};
       }
     }
+    cx<A> u[9];
+    load_link9<P, true>(u, lraw, 32, lane, D);
+    hop_term_u<P, MU>(acc, psi, u, sgn);
   }
 }
 
-// acc += sum over live directions d of the hop from element nb[d] * NB + eg of `in`.
-template <int P, bool DAG>
-__device__ __forceinline__ void simd_hop(Spinor<typename Prec<P>::acc>& acc,
-                                         const uint32_t (&nb)[8], uint32_t live, const void* in,
-                                         long stride, int NB, long eg, int s,
-                                         const cx<typename Prec<P>::acc>* lk, int lane) {
-  using A = typename Prec<P>::acc;
+// acc += sum over the live directions of the hop from `in` (element nb * NB + eg) with the
+// tile's links in lraw.  16-bit and FP32: the neighbour spinors go through a two-slot
+// cp.async ring in shared memory, so the copy of the next live direction is in flight while
+// the current one is computed (each thread reads back only its own copies: no block barrier).
+template <int P, int LS, bool DAG>
+__device__ __forceinline__ void simd_hop(Spinor<typename Prec<P>::acc>& acc, const uint32_t* row,
+                                         uint32_t live, const void* in, long stride, int NB,
+                                         long eg, int s, const uint4* lraw, uint4* ring,
+                                         int lane, int tid) {
+  constexpr int NCH = Prec<P>::NCH;
+  constexpr int NT = 32 * LS;
+  if constexpr (!simd_ring<P>()) {
 #pragma unroll
-  for (int d = 0; d < 8; d++) {
-    if (!((live >> d) & 1u)) continue;
-    Spinor<A> psi;
-    ld_spinor<P>(psi, in, stride, (long)nb[d] * NB + eg, s);
-    cx<A> u[9];
+    for (int d = 0; d < 8; d++) {
+      if (!((live >> d) & 1u)) continue;
+      const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)s * NCH) * stride +
+                       (long)__ldg(row + d) * NB + eg;
+      uint4 v[NCH];
 #pragma unroll
-    for (int k = 0; k < 9; k++) u[k] = lk[(d * 9 + k) * 32 + lane];
-    // forward hop (1 - gamma_mu), backward (1 + gamma_mu); the adjoint swaps them
-    const A sgn = (((d & 1) != 0) != DAG) ? A(1) : A(-1);
-    switch (d >> 1) {
-      case 0: hop_term_u<P, 0>(acc, psi, u, sgn); break;
-      case 1: hop_term_u<P, 1>(acc, psi, u, sgn); break;
-      case 2: hop_term_u<P, 2>(acc, psi, u, sgn); break;
-      default: hop_term_u<P, 3>(acc, psi, u, sgn); break;
+      for (int k = 0; k < NCH; k++) v[k] = __ldcg(q + k * stride);
+      switch (d) {
+        case 0: simd_term<P, 0, DAG, 0>(acc, v, 1, lraw, lane); break;
+        case 1: simd_term<P, 0, DAG, 1>(acc, v, 1, lraw, lane); break;
+        case 2: simd_term<P, 1, DAG, 2>(acc, v, 1, lraw, lane); break;
+        case 3: simd_term<P, 1, DAG, 3>(acc, v, 1, lraw, lane); break;
+        case 4: simd_term<P, 2, DAG, 4>(acc, v, 1, lraw, lane); break;
+        case 5: simd_term<P, 2, DAG, 5>(acc, v, 1, lraw, lane); break;
+        case 6: simd_term<P, 3, DAG, 6>(acc, v, 1, lraw, lane); break;
+        default: simd_term<P, 3, DAG, 7>(acc, v, 1, lraw, lane); break;
+      }
+    }
+  } else {
+    auto issue = [&](int d, int slot) {
+      const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)s * NCH) * stride +
+                       (long)__ldg(row + d) * NB + eg;
+      uint4* dst = ring + (slot * NCH) * NT + tid;
+#pragma unroll
+      for (int k = 0; k < NCH; k++) cp_async16<false>(dst + k * NT, q + k * stride);
+      cp_async_commit();
+    };
+    if (!live) return;
+    int slot = 0;
+    issue(__ffs(live) - 1, 0);
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+      if (!((live >> d) & 1u)) continue;
+      const uint32_t later = live & ~((2u << d) - 1u);
+      if (later) {
+        issue(__ffs(later) - 1, slot ^ 1);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      const uint4* q = ring + (slot * NCH) * NT + tid;
+      switch (d) {
+        case 0: simd_term<P, 0, DAG, 0>(acc, q, NT, lraw, lane); break;
+        case 1: simd_term<P, 0, DAG, 1>(acc, q, NT, lraw, lane); break;
+        case 2: simd_term<P, 1, DAG, 2>(acc, q, NT, lraw, lane); break;
+        case 3: simd_term<P, 1, DAG, 3>(acc, q, NT, lraw, lane); break;
+        case 4: simd_term<P, 2, DAG, 4>(acc, q, NT, lraw, lane); break;
+        case 5: simd_term<P, 2, DAG, 5>(acc, q, NT, lraw, lane); break;
+        case 6: simd_term<P, 3, DAG, 6>(acc, q, NT, lraw, lane); break;
+        default: simd_term<P, 3, DAG, 7>(acc, q, NT, lraw, lane); break;
+      }
+      slot ^= 1;
     }
   }
 }
@@ -361,9 +447,12 @@ template <int P, int LS>
 __global__ void __launch_bounds__(32 * LS, (P == P64) ? 1 : 2)
 simd_local_kernel(const SimdArgs a) {
   using A = typename Prec<P>::acc;
-  extern __shared__ __align__(16) unsigned char smem[];
-  cx<A>* lk = reinterpret_cast<cx<A>*>(smem);                    // [8][9][32]
-  A* buf = reinterpret_cast<A*>(smem + 8 * 9 * 32 * sizeof(cx<A>));   // [LS][24][32]
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint4* lraw0 = reinterpret_cast<uint4*>(smem);
+  uint4* lraw1 = reinterpret_cast<uint4*>(smem + simd_lraw_bytes<P>());
+  unsigned char* region = smem + 2 * simd_lraw_bytes<P>();
+  uint4* ring = reinterpret_cast<uint4*>(region);   // during the hops
+  A* buf = reinterpret_cast<A*>(region);            // afterwards
   __shared__ A red[LS][32];
   __shared__ double sc[32];
   constexpr int NT = 32 * LS;
@@ -381,9 +470,39 @@ simd_local_kernel(const SimdArgs a) {
     ++nbar;
     return slot_barrier(ctr, nbar * (unsigned)C, a.wait_ns, a.err);
   };
+  // One hop phase over the schedule `sch` (n positions) of output tables `tab`: the tile's
+  // links are prefetched one tile ahead into the idle raw buffer; `body(pos, row, live, lraw)`
+  // computes the tile.
+  auto phase = [&](const int* sch, int n, const uint32_t* tab, bool be_only, const void* links,
+                   long lstride, long eg0, auto body) {
+    int it = 0;
+    if (ci < n) {
+      const int pos = __ldg(sch + ci);
+      simd_prefetch_links<P>(lraw0, links, lstride, (long)pos * NB + eg0,
+                             simd_live(tab + pos * 8, be_only, a.nBE), tid, NT);
+    }
+    for (int i = ci; i < n; i += C, it++) {
+      const int pos = __ldg(sch + i);
+      const uint32_t* row = tab + pos * 8;
+      const uint32_t live = simd_live(row, be_only, a.nBE);
+      uint4* cur = (it & 1) ? lraw1 : lraw0;
+      uint4* nxt = (it & 1) ? lraw0 : lraw1;
+      cp_async_wait<0>();
+      __syncthreads();   // every thread's link copies of this tile have landed
+      if (i + C < n) {
+        const int pn = __ldg(sch + i + C);
+        simd_prefetch_links<P>(nxt, links, lstride, (long)pn * NB + eg0,
+                               simd_live(tab + pn * 8, be_only, a.nBE), tid, NT);
+      }
+      body(pos, row, live, cur);
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+  };
 
   for (int g = slot; g < a.ngroups; g += a.nslots) {
-    const long eg = (long)g * 32 + lane;   // this lane's block, as an element offset
+    const long eg0 = (long)g * 32;
+    const long eg = eg0 + lane;   // this lane's block, as an element offset
     double rho, alpha = 0.0, beta = 0.0;
     // ---- P0: r = f r_outer (gathered into the block layout), p = r, x = 0, u = D+ p
     {
@@ -428,53 +547,38 @@ simd_local_kernel(const SimdArgs a) {
     for (int k = 0; k < a.l; k++) {
       const bool last = (k + 1 == a.l);
       // ---- P1: t = [D+ M5op^-1] Dh_oe (D+ p) on O
-      for (int i = ci; i < a.nsch[0]; i += C) {
-        const int pos = __ldg(a.sch[0] + i);
-        uint32_t nb[8], live = 0;
-#pragma unroll
-        for (int d = 0; d < 8; d++) {
-          nb[d] = __ldg(a.nbrO + pos * 8 + d);
-          if (nb[d] != SIMD_ABSENT && nb[d] < (uint32_t)a.nBE) live |= 1u << d;
-        }
-        simd_stage_links<P>(lk, a.linksO, sO, (long)pos * NB + (long)g * 32, live, tid, NT);
-        __syncthreads();
-        Spinor<A> acc;
-        zero(acc);
-        simd_hop<P, false>(acc, nb, live, pin1, sB, NB, eg, s, lk, lane);
-        to_buf(buf, acc, s, lane);
-        __syncthreads();
-        post_recurrence<A, LS, false>(buf, K, tid, NT);
-        __syncthreads();
-        from_buf(acc, buf, s, lane);
-        store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
-        __syncthreads();
-      }
+      phase(a.sch[0], a.nsch[0], a.nbrO, true, a.linksO, sO, eg0,
+            [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
+              Spinor<A> acc;
+              zero(acc);
+              simd_hop<P, LS, false>(acc, row, live, pin1, sB, NB, eg, s, lraw, ring, lane,
+                                     tid);
+              __syncthreads();   // the ring becomes the post buffer
+              to_buf(buf, acc, s, lane);
+              __syncthreads();
+              post_recurrence<A, LS, false>(buf, K, tid, NT);
+              __syncthreads();
+              from_buf(acc, buf, s, lane);
+              store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
+            });
       if (!barrier()) return;
       // ---- P2: y = M5op p - 1/4 Dh_eo t on E; <p, A_s p> = ||y||^2 over the block
       {
         A nrm = A(0);
         const A hs = A(-0.25);
-        for (int i = ci; i < a.nsch[1]; i += C) {
-          const int pos = __ldg(a.sch[1] + i);
-          uint32_t nb[8], live = 0;
+        phase(a.sch[1], a.nsch[1], a.nbrE, false, a.linksE, sE, eg0,
+              [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
+                Spinor<A> acc;
+                zero(acc);
+                simd_hop<P, LS, false>(acc, row, live, a.t, sO, NB, eg, s, lraw, ring, lane,
+                                       tid);
 #pragma unroll
-          for (int d = 0; d < 8; d++) {
-            nb[d] = __ldg(a.nbrE + pos * 8 + d);
-            if (nb[d] != SIMD_ABSENT) live |= 1u << d;
-          }
-          simd_stage_links<P>(lk, a.linksE, sE, (long)pos * NB + (long)g * 32, live, tid, NT);
-          __syncthreads();
-          Spinor<A> acc;
-          zero(acc);
-          simd_hop<P, false>(acc, nb, live, a.t, sO, NB, eg, s, lk, lane);
-#pragma unroll
-          for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
-          const long e = (long)pos * NB + eg;
-          if (pos < a.nBE) add_m5<P, false>(acc, a.p, sB, e, s, LS, K);
-          nrm += norm2(acc);
-          if (!last) store_spinor<P>(a.y, sE, e, s, acc);
-          __syncthreads();
-        }
+                for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
+                const long e = (long)pos * NB + eg;
+                if (pos < a.nBE) add_m5<P, false>(acc, a.p, sB, e, s, LS, K);
+                nrm += norm2(acc);
+                if (!last) store_spinor<P>(a.y, sE, e, s, acc);
+              });
         write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
         if (!barrier()) return;
         const double pap = slot_total(part, C, sc, s, lane);
@@ -498,62 +602,49 @@ simd_local_kernel(const SimdArgs a) {
         break;
       }
       // ---- P3: s = [M5op^-dag D+^dag] Dh_oe^dag y on O
-      for (int i = ci; i < a.nsch[2]; i += C) {
-        const int pos = __ldg(a.sch[2] + i);
-        uint32_t nb[8], live = 0;
-#pragma unroll
-        for (int d = 0; d < 8; d++) {
-          nb[d] = __ldg(a.nbrO + pos * 8 + d);
-          if (nb[d] != SIMD_ABSENT) live |= 1u << d;
-        }
-        simd_stage_links<P>(lk, a.linksO, sO, (long)pos * NB + (long)g * 32, live, tid, NT);
-        __syncthreads();
-        Spinor<A> acc;
-        zero(acc);
-        simd_hop<P, true>(acc, nb, live, a.y, sE, NB, eg, s, lk, lane);
-        to_buf(buf, acc, s, lane);
-        __syncthreads();
-        post_recurrence<A, LS, true>(buf, K, tid, NT);
-        __syncthreads();
-        from_buf(acc, buf, s, lane);
-        store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
-        __syncthreads();
-      }
+      phase(a.sch[2], a.nsch[2], a.nbrO, false, a.linksO, sO, eg0,
+            [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
+              Spinor<A> acc;
+              zero(acc);
+              simd_hop<P, LS, true>(acc, row, live, a.y, sE, NB, eg, s, lraw, ring, lane, tid);
+              __syncthreads();
+              to_buf(buf, acc, s, lane);
+              __syncthreads();
+              post_recurrence<A, LS, true>(buf, K, tid, NT);
+              __syncthreads();
+              from_buf(acc, buf, s, lane);
+              store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
+            });
       if (!barrier()) return;
       // ---- P4: r -= alpha (M5op^dag y - 1/4 D+^dag Dh_eo^dag s) on BE; ||r||^2 -> beta
       {
         A nrm = A(0);
         const A al = A(alpha), hs = A(a.hs_b);
-        for (int i = ci; i < a.nsch[3]; i += C) {
-          const int pos = __ldg(a.sch[3] + i);
-          uint32_t nb[8], live = 0;
+        phase(a.sch[3], a.nsch[3], a.nbrE, false, a.linksE, sE, eg0,
+              [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
+                Spinor<A> acc;
+                zero(acc);
+                simd_hop<P, LS, true>(acc, row, live, a.t, sO, NB, eg, s, lraw, ring, lane,
+                                      tid);
+                if (!a.trivial) {
+                  __syncthreads();   // the ring becomes the slice-exchange buffer
+                  dplus_slices<A, LS, true>(acc, buf, K, s, lane);
+                }
 #pragma unroll
-          for (int d = 0; d < 8; d++) {
-            nb[d] = __ldg(a.nbrE + pos * 8 + d);
-            if (nb[d] != SIMD_ABSENT) live |= 1u << d;
-          }
-          simd_stage_links<P>(lk, a.linksE, sE, (long)pos * NB + (long)g * 32, live, tid, NT);
-          __syncthreads();
-          Spinor<A> acc;
-          zero(acc);
-          simd_hop<P, true>(acc, nb, live, a.t, sO, NB, eg, s, lk, lane);
-          if (!a.trivial) dplus_slices<A, LS, true>(acc, buf, K, s, lane);
+                for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
+                const long e = (long)pos * NB + eg;
+                add_m5<P, true>(acc, a.y, sE, e, s, LS, K);
+                Spinor<A> rr;
+                ld_spinor<P>(rr, a.r, sB, e, s);
 #pragma unroll
-          for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
-          const long e = (long)pos * NB + eg;
-          add_m5<P, true>(acc, a.y, sE, e, s, LS, K);
-          Spinor<A> rr;
-          ld_spinor<P>(rr, a.r, sB, e, s);
-#pragma unroll
-          for (int q = 0; q < 12; q++) {
-            rr.c[q].x -= al * acc.c[q].x;
-            rr.c[q].y -= al * acc.c[q].y;
-          }
-          store_spinor<P>(a.r, sB, e, s, rr);
-          round_to_storage<P>(rr);
-          nrm += norm2(rr);
-          __syncthreads();
-        }
+                for (int q = 0; q < 12; q++) {
+                  rr.c[q].x -= al * acc.c[q].x;
+                  rr.c[q].y -= al * acc.c[q].y;
+                }
+                store_spinor<P>(a.r, sB, e, s, rr);
+                round_to_storage<P>(rr);
+                nrm += norm2(rr);
+              });
         write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
         if (!barrier()) return;
         const double rr_new = slot_total(part, C, sc, s, lane);

@@ -13,8 +13,7 @@ template <int P, int LS>
 static cudaError_t launch_ls(const SimdArgs& a, int* grid_cap, int nsm, cudaStream_t st,
                              bool query) {
   auto k = simd_local_kernel<P, LS>;
-  using A = typename Prec<P>::acc;
-  const size_t smem = 8 * 9 * 32 * sizeof(cx<A>) + (size_t)LS * 24 * 32 * sizeof(A);
+  const size_t smem = simd_smem_bytes<P>(LS);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
