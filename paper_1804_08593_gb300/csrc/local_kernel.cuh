@@ -16,7 +16,10 @@
 //
 // Work split.  Blocks come in groups of 32 (one lane each); a fixed set of C CTAs (a "slot")
 // runs every phase of every iteration of its block groups, each CTA taking positions from a
-// cost-sorted schedule in round robin.  Phases of one CG iteration on A_s = Mpc_s^dag Mpc_s:
+// cost-sorted schedule in round robin.  A CTA is 32 lanes x Ls/NSL warps; each thread handles
+// NSL fifth-dimension slices (two for FP32/FP16/BF16: slices w and w + Ls/2 share every link
+// load and run the SU(3) products in packed f32x2 arithmetic; one for FP64).  Phases of one CG
+// iteration on A_s = Mpc_s^dag Mpc_s:
 //   P1  t = [D+ M5op^-1] Dh_oe (D+ p)        on O  (input on BE)
 //   P2  y = M5op p - 1/4 Dh_eo t             on E, per-block ||y||^2 = <p, A_s p> -> alpha
 //   P3  s = [M5op^-dag D+^dag] Dh_oe^dag y   on O
@@ -28,6 +31,8 @@
 // (deterministic, and every CTA holds the same alpha and beta).  The launch is cooperative, so
 // all CTAs are resident at once.
 #pragma once
+
+#include <type_traits>
 
 #include "dwf_device.cuh"
 #include "stage.cuh"
@@ -72,6 +77,10 @@ __device__ __forceinline__ Coef5<A> simd_coef(const SimdArgs& a) {
   if constexpr (sizeof(A) == 8) return a.k64; else return a.k32;
 }
 
+// slices per thread
+template <int P>
+__host__ __device__ constexpr int simd_nsl() { return P == P64 ? 1 : 2; }
+
 // Spinor of element e, slice s, from a field written earlier in this kernel (loads through
 // L2: another SM may have written it since this SM last cached the line).
 template <int P>
@@ -108,8 +117,8 @@ __device__ __forceinline__ void ld_spinor(Spinor<typename Prec<P>::acc>& out, co
 
 // Shared memory of the local-solve kernel: two buffers of raw tile links ([8][NCHL][32] chunks
 // of 16 bytes; the next tile's links are copied in while the current tile computes), then one
-// region used first as the per-thread neighbour ring ([2][NCH][32 LS] chunks; not for FP64,
-// which loads neighbours directly) and then as the fifth-dimension buffer ([LS][24][32]).
+// region used first as the per-thread neighbour ring ([2][NSL][NCH][threads] chunks; not for
+// FP64, which loads neighbours directly) and then as the fifth-dimension buffer ([LS][24][32]).
 template <int P>
 __host__ __device__ constexpr size_t simd_lraw_bytes() {
   return (size_t)8 * Prec<P>::NCHL * 32 * 16;
@@ -154,75 +163,143 @@ __device__ __forceinline__ uint32_t simd_live(const uint32_t* row, bool be_only,
   return live;
 }
 
-template <int P, int MU, bool DAG, int D>
-__device__ __forceinline__ void simd_term(Spinor<typename Prec<P>::acc>& acc, const uint4* q,
-                                          int qs, const uint4* lraw, int lane) {
-  using A = typename Prec<P>::acc;
-  constexpr bool back = (D & 1) != 0;
-  const A sgn = (back != DAG) ? A(1) : A(-1);
-  if constexpr (P == P16 || P == PB16) {
-    const uint4 qq[3] = {q[0], q[qs], q[2 * qs]};
-    hop_term16<P, MU, true>(acc, qq, lraw + (D * 3) * 32 + lane, 32, sgn);
-  } else {
-    Spinor<A> psi;
-    if constexpr (P == P32) {
+// The spinor of NCH 16-byte chunks q[0], q[qs], ... in the accumulation type.
+template <int P>
+__device__ __forceinline__ void unpack_chunks(Spinor<typename Prec<P>::acc>& psi, const uint4* q,
+                                              int qs) {
+  if constexpr (P == P64) {
 #pragma unroll
-      for (int k = 0; k < 6; k++) {
-        const float4 v = *reinterpret_cast<const float4*>(q + k * qs);
-        psi.c[2 * k] = {v.x, v.y};
-        psi.c[2 * k + 1] = {v.z, v.w};
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 12; k++) {
-        const double2 v = *reinterpret_cast<const double2*>(q + k * qs);
-        psi.c[k] = {v.x, v.y};
-      }
+    for (int k = 0; k < 12; k++) {
+      const double2 v = *reinterpret_cast<const double2*>(q + k * qs);
+      psi.c[k] = {v.x, v.y};
     }
-    cx<A> u[9];
-    load_link9<P, true>(u, lraw, 32, lane, D);
-    hop_term_u<P, MU>(acc, psi, u, sgn);
+  } else if constexpr (P == P32) {
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const float4 v = *reinterpret_cast<const float4*>(q + k * qs);
+      psi.c[2 * k] = {v.x, v.y};
+      psi.c[2 * k + 1] = {v.z, v.w};
+    }
+  } else {
+    constexpr bool BF = (P == PB16);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint4 v = q[k * qs];
+      const float2 a = h2f(v.x, BF), b = h2f(v.y, BF), c = h2f(v.z, BF), d = h2f(v.w, BF);
+      psi.c[4 * k] = {a.x, a.y};
+      psi.c[4 * k + 1] = {b.x, b.y};
+      psi.c[4 * k + 2] = {c.x, c.y};
+      psi.c[4 * k + 3] = {d.x, d.y};
+    }
   }
 }
 
-// acc += sum over the live directions of the hop from `in` (element nb * NB + eg) with the
-// tile's links in lraw.  16-bit and FP32: the neighbour spinors go through a two-slot
-// cp.async ring in shared memory, so the copy of the next live direction is in flight while
-// the current one is computed (each thread reads back only its own copies: no block barrier).
+// Accumulator of a thread's NSL slices: FP64 one Spinor, the others packed pairs (cx2: the
+// two slices' components side by side in float2 registers).
+template <int P>
+struct HopAcc {
+  cx2 c[12];
+};
+template <>
+struct HopAcc<P64> {
+  Spinor<double> s;
+};
+
+template <int P>
+__device__ __forceinline__ void hop_acc_zero(HopAcc<P>& h) {
+  if constexpr (P == P64) {
+    zero(h.s);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) h.c[k] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  }
+}
+template <int P, int NSL>
+__device__ __forceinline__ void hop_acc_out(const HopAcc<P>& h,
+                                            Spinor<typename Prec<P>::acc> (&out)[NSL]) {
+  if constexpr (P == P64) {
+    out[0] = h.s;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      out[0].c[k] = {h.c[k].x.x, h.c[k].y.x};
+      out[1].c[k] = {h.c[k].x.y, h.c[k].y.y};
+    }
+  }
+}
+
+// One hop direction D for the thread's slices: spinors from the chunks at q (slice j at
+// q + j * jstride, chunk k at + k * qs), the link from the tile's raw copy.
+template <int P, bool DAG, int D>
+__device__ __forceinline__ void simd_term(HopAcc<P>& acc, const uint4* q, int qs, int jstride,
+                                          const uint4* lraw, int lane) {
+  using A = typename Prec<P>::acc;
+  constexpr bool back = (D & 1) != 0;
+  const A sgn = (back != DAG) ? A(1) : A(-1);
+  cx<A> u[9];
+  load_link9<P, true>(u, lraw, 32, lane, D);
+  if constexpr (P == P64) {
+    Spinor<A> psi;
+    unpack_chunks<P>(psi, q, qs);
+    hop_term_u<P, D / 2>(acc.s, psi, u, sgn);
+  } else {
+    Spinor<float> psi0, psi1;
+    unpack_chunks<P>(psi0, q, qs);
+    unpack_chunks<P>(psi1, q + jstride, qs);
+    hop_term_f2<D / 2>(acc.c, psi0, psi1, u, sgn);
+  }
+}
+
+template <int P, bool DAG>
+__device__ __forceinline__ void simd_term_d(int d, HopAcc<P>& acc, const uint4* q, int qs,
+                                            int jstride, const uint4* lraw, int lane) {
+  switch (d) {
+    case 0: simd_term<P, DAG, 0>(acc, q, qs, jstride, lraw, lane); break;
+    case 1: simd_term<P, DAG, 1>(acc, q, qs, jstride, lraw, lane); break;
+    case 2: simd_term<P, DAG, 2>(acc, q, qs, jstride, lraw, lane); break;
+    case 3: simd_term<P, DAG, 3>(acc, q, qs, jstride, lraw, lane); break;
+    case 4: simd_term<P, DAG, 4>(acc, q, qs, jstride, lraw, lane); break;
+    case 5: simd_term<P, DAG, 5>(acc, q, qs, jstride, lraw, lane); break;
+    case 6: simd_term<P, DAG, 6>(acc, q, qs, jstride, lraw, lane); break;
+    default: simd_term<P, DAG, 7>(acc, q, qs, jstride, lraw, lane); break;
+  }
+}
+
+// acc += sum over the live directions of the hop from `in` (element nb * NB + eg) for the
+// thread's slices w (+ LS/2), with the tile's links in lraw.  16-bit and FP32: the neighbour
+// spinors go through a two-slot cp.async ring in shared memory, so the copy of the next live
+// direction is in flight while the current one is computed (each thread reads back only its
+// own copies: no block barrier).
 template <int P, int LS, bool DAG>
-__device__ __forceinline__ void simd_hop(Spinor<typename Prec<P>::acc>& acc, const uint32_t* row,
-                                         uint32_t live, const void* in, long stride, int NB,
-                                         long eg, int s, const uint4* lraw, uint4* ring,
-                                         int lane, int tid) {
+__device__ __forceinline__ void simd_hop(HopAcc<P>& acc, const uint32_t* row, uint32_t live,
+                                         const void* in, long stride, int NB, long eg, int w,
+                                         const uint4* lraw, uint4* ring, int lane, int tid) {
   constexpr int NCH = Prec<P>::NCH;
-  constexpr int NT = 32 * LS;
+  constexpr int NSL = simd_nsl<P>();
+  constexpr int LSP = LS / NSL;
+  constexpr int NT = 32 * LSP;
   if constexpr (!simd_ring<P>()) {
 #pragma unroll
     for (int d = 0; d < 8; d++) {
       if (!((live >> d) & 1u)) continue;
-      const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)s * NCH) * stride +
+      const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)w * NCH) * stride +
                        (long)__ldg(row + d) * NB + eg;
       uint4 v[NCH];
 #pragma unroll
       for (int k = 0; k < NCH; k++) v[k] = __ldcg(q + k * stride);
-      switch (d) {
-        case 0: simd_term<P, 0, DAG, 0>(acc, v, 1, lraw, lane); break;
-        case 1: simd_term<P, 0, DAG, 1>(acc, v, 1, lraw, lane); break;
-        case 2: simd_term<P, 1, DAG, 2>(acc, v, 1, lraw, lane); break;
-        case 3: simd_term<P, 1, DAG, 3>(acc, v, 1, lraw, lane); break;
-        case 4: simd_term<P, 2, DAG, 4>(acc, v, 1, lraw, lane); break;
-        case 5: simd_term<P, 2, DAG, 5>(acc, v, 1, lraw, lane); break;
-        case 6: simd_term<P, 3, DAG, 6>(acc, v, 1, lraw, lane); break;
-        default: simd_term<P, 3, DAG, 7>(acc, v, 1, lraw, lane); break;
-      }
+      simd_term_d<P, DAG>(d, acc, v, 1, 0, lraw, lane);
     }
   } else {
+    // ring slot layout: [slot][slice j][chunk k][thread]
     auto issue = [&](int d, int slot) {
-      const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)s * NCH) * stride +
+      const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)w * NCH) * stride +
                        (long)__ldg(row + d) * NB + eg;
-      uint4* dst = ring + (slot * NCH) * NT + tid;
+      uint4* dst = ring + (slot * NSL * NCH) * NT + tid;
 #pragma unroll
-      for (int k = 0; k < NCH; k++) cp_async16<false>(dst + k * NT, q + k * stride);
+      for (int j = 0; j < NSL; j++)
+#pragma unroll
+        for (int k = 0; k < NCH; k++)
+          cp_async16<false>(dst + (j * NCH + k) * NT, q + ((long)j * LSP * NCH + k) * stride);
       cp_async_commit();
     };
     if (!live) return;
@@ -238,20 +315,23 @@ __device__ __forceinline__ void simd_hop(Spinor<typename Prec<P>::acc>& acc, con
       } else {
         cp_async_wait<0>();
       }
-      const uint4* q = ring + (slot * NCH) * NT + tid;
-      switch (d) {
-        case 0: simd_term<P, 0, DAG, 0>(acc, q, NT, lraw, lane); break;
-        case 1: simd_term<P, 0, DAG, 1>(acc, q, NT, lraw, lane); break;
-        case 2: simd_term<P, 1, DAG, 2>(acc, q, NT, lraw, lane); break;
-        case 3: simd_term<P, 1, DAG, 3>(acc, q, NT, lraw, lane); break;
-        case 4: simd_term<P, 2, DAG, 4>(acc, q, NT, lraw, lane); break;
-        case 5: simd_term<P, 2, DAG, 5>(acc, q, NT, lraw, lane); break;
-        case 6: simd_term<P, 3, DAG, 6>(acc, q, NT, lraw, lane); break;
-        default: simd_term<P, 3, DAG, 7>(acc, q, NT, lraw, lane); break;
-      }
+      const uint4* q = ring + (slot * NSL * NCH) * NT + tid;
+      simd_term_d<P, DAG>(d, acc, q, NT, NCH * NT, lraw, lane);
       slot ^= 1;
     }
   }
+}
+
+// The hop of the tile, unpacked into one spinor per slice of the thread.
+template <int P, int LS, bool DAG>
+__device__ __forceinline__ void simd_hop_out(Spinor<typename Prec<P>::acc> (&out)[simd_nsl<P>()],
+                                             const uint32_t* row, uint32_t live, const void* in,
+                                             long stride, int NB, long eg, int w,
+                                             const uint4* lraw, uint4* ring, int lane, int tid) {
+  HopAcc<P> h;
+  hop_acc_zero<P>(h);
+  simd_hop<P, LS, DAG>(h, row, live, in, stride, NB, eg, w, lraw, ring, lane, tid);
+  hop_acc_out<P, simd_nsl<P>()>(h, out);
 }
 
 // buf[s][24][32] <-> the per-thread spinor of slice s
@@ -334,23 +414,29 @@ __device__ __forceinline__ void post_recurrence(A* buf, const Coef5<A>& C, int t
   }
 }
 
-// v <- D+ v (P+ spins from s-1, P- spins from s+1, -mf at the walls), or D+^dag v (P+ from
-// s+1, P- from s-1), through the slices' copies in buf (which this call fills).
-template <typename A, int LS, bool DAG>
-__device__ __forceinline__ void dplus_slices(Spinor<A>& v, A* buf, const Coef5<A>& C, int s,
-                                             int lane) {
-  to_buf(buf, v, s, lane);
-  __syncthreads();
-  const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
-  const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
+// v[j] <- D+ v[j] (P+ spins from s-1, P- spins from s+1, -mf at the walls), or D+^dag (P+ from
+// s+1, P- from s-1), for the thread's slices s_j = w + j LS/NSL, through buf (filled here).
+template <typename A, int LS, int NSL, bool DAG>
+__device__ __forceinline__ void dplus_slices(Spinor<A> (&v)[NSL], A* buf, const Coef5<A>& C,
+                                             int w, int lane) {
+  constexpr int LSP = LS / NSL;
 #pragma unroll
-  for (int k = 0; k < 12; k++) {
-    const bool plus = k < 6;
-    const bool from_up = DAG ? plus : !plus;
-    const int sn = from_up ? su : sd;
-    const A f = from_up ? fu : fd;
-    v.c[k].x = C.db * v.c[k].x + C.dc * f * buf[(sn * 24 + 2 * k) * 32 + lane];
-    v.c[k].y = C.db * v.c[k].y + C.dc * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+  for (int j = 0; j < NSL; j++) to_buf(buf, v[j], w + j * LSP, lane);
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NSL; j++) {
+    const int s = w + j * LSP;
+    const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
+    const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const bool plus = k < 6;
+      const bool from_up = DAG ? plus : !plus;
+      const int sn = from_up ? su : sd;
+      const A f = from_up ? fu : fd;
+      v[j].c[k].x = C.db * v[j].c[k].x + C.dc * f * buf[(sn * 24 + 2 * k) * 32 + lane];
+      v[j].c[k].y = C.db * v[j].c[k].y + C.dc * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+    }
   }
   __syncthreads();
 }
@@ -416,23 +502,23 @@ __device__ __forceinline__ bool slot_barrier(unsigned* ctr, unsigned target,
   return ok_s != 0;
 }
 
-// One FP64 partial per (CTA, lane) of the thread-level values v (summed over the slices).
-template <typename A, int LS>
-__device__ __forceinline__ void write_partial(A v, A (*red)[32], double* dst, int s, int lane) {
-  red[s][lane] = v;
+// One FP64 partial per (CTA, lane) of the thread-level values v (summed over the warps).
+template <typename A, int NW>
+__device__ __forceinline__ void write_partial(A v, A (*red)[32], double* dst, int w, int lane) {
+  red[w][lane] = v;
   __syncthreads();
-  if (s == 0) {
+  if (w == 0) {
     double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < LS; w++) t += (double)red[w][lane];
+    for (int k = 0; k < NW; k++) t += (double)red[k][lane];
     dst[lane] = t;
   }
 }
 
 // Sum over the slot's C partials of this lane's block (fixed order); valid in every thread.
-__device__ __forceinline__ double slot_total(const double* part, int C, double* sc, int s,
+__device__ __forceinline__ double slot_total(const double* part, int C, double* sc, int w,
                                              int lane) {
-  if (s == 0) {
+  if (w == 0) {
     double t = 0.0;
     for (int c = 0; c < C; c++) t += __ldcg(part + c * 32 + lane);
     sc[lane] = t;
@@ -444,19 +530,21 @@ __device__ __forceinline__ double slot_total(const double* part, int C, double* 
 }
 
 template <int P, int LS>
-__global__ void __launch_bounds__(32 * LS, (P == P64) ? 1 : 2)
+__global__ void __launch_bounds__(32 * LS / simd_nsl<P>(), (P == P64) ? 1 : 2)
 simd_local_kernel(const SimdArgs a) {
   using A = typename Prec<P>::acc;
+  constexpr int NSL = simd_nsl<P>();
+  constexpr int LSP = LS / NSL;    // warps; thread (lane, w) handles slices w + j LSP
+  constexpr int NT = 32 * LSP;
   extern __shared__ __align__(128) unsigned char smem[];
   uint4* lraw0 = reinterpret_cast<uint4*>(smem);
   uint4* lraw1 = reinterpret_cast<uint4*>(smem + simd_lraw_bytes<P>());
   unsigned char* region = smem + 2 * simd_lraw_bytes<P>();
   uint4* ring = reinterpret_cast<uint4*>(region);   // during the hops
   A* buf = reinterpret_cast<A*>(region);            // afterwards
-  __shared__ A red[LS][32];
+  __shared__ A red[LSP][32];
   __shared__ double sc[32];
-  constexpr int NT = 32 * LS;
-  const int lane = threadIdx.x, s = threadIdx.y, tid = lane + 32 * s;
+  const int lane = threadIdx.x, w = threadIdx.y, tid = lane + 32 * w;
   const int C = a.C, slot = blockIdx.x / C, ci = blockIdx.x % C;
   if (slot >= a.nslots) return;
   unsigned* ctr = a.ctr + slot;
@@ -512,54 +600,60 @@ simd_local_kernel(const SimdArgs a) {
       for (int pos = ci; pos < a.nBE; pos += C) {
         const long e = (long)pos * NB + eg;
         const int o = __ldg(a.fwd + e);
-        Spinor<A> v;
-        if (o < 0) {
-          zero(v);
-        } else if (a.prec_outer == P64) {
-          Spinor<double> w;
-          load_spinor<P64>(w, a.r_outer, a.Vp_outer, o, s);
+        Spinor<A> v[NSL];
 #pragma unroll
-          for (int k = 0; k < 12; k++) v.c[k] = {A(w.c[k].x * f), A(w.c[k].y * f)};
-        } else {
-          Spinor<float> w;
-          load_spinor<P32>(w, a.r_outer, a.Vp_outer, o, s);
-          const A ff = A(f);
+        for (int j = 0; j < NSL; j++) {
+          const int s = w + j * LSP;
+          if (o < 0) {
+            zero(v[j]);
+          } else if (a.prec_outer == P64) {
+            Spinor<double> q;
+            load_spinor<P64>(q, a.r_outer, a.Vp_outer, o, s);
 #pragma unroll
-          for (int k = 0; k < 12; k++) v.c[k] = {A(w.c[k].x) * ff, A(w.c[k].y) * ff};
+            for (int k = 0; k < 12; k++) v[j].c[k] = {A(q.c[k].x * f), A(q.c[k].y * f)};
+          } else {
+            Spinor<float> q;
+            load_spinor<P32>(q, a.r_outer, a.Vp_outer, o, s);
+            const A ff = A(f);
+#pragma unroll
+            for (int k = 0; k < 12; k++) v[j].c[k] = {A(q.c[k].x) * ff, A(q.c[k].y) * ff};
+          }
+          store_spinor<P>(a.r, sB, e, s, v[j]);
+          store_spinor<P>(a.p, sB, e, s, v[j]);
+          Spinor<A> zz;
+          zero(zz);
+          store_spinor<P>(a.x, sB, e, s, zz);
+          round_to_storage<P>(v[j]);
+          nrm += norm2(v[j]);
         }
-        store_spinor<P>(a.r, sB, e, s, v);
-        store_spinor<P>(a.p, sB, e, s, v);
-        Spinor<A> zz;
-        zero(zz);
-        store_spinor<P>(a.x, sB, e, s, zz);
-        Spinor<A> back = v;
-        round_to_storage<P>(back);
-        nrm += norm2(back);
         if (!a.trivial) {
-          dplus_slices<A, LS, false>(back, buf, K, s, lane);
-          store_spinor<P>(a.u, sB, e, s, back);
+          dplus_slices<A, LS, NSL, false>(v, buf, K, w, lane);
+#pragma unroll
+          for (int j = 0; j < NSL; j++) store_spinor<P>(a.u, sB, e, w + j * LSP, v[j]);
         }
       }
-      write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
+      write_partial<A, LSP>(nrm, red, part + ci * 32, w, lane);
       if (!barrier()) return;
-      rho = slot_total(part, C, sc, s, lane);
+      rho = slot_total(part, C, sc, w, lane);
     }
     for (int k = 0; k < a.l; k++) {
       const bool last = (k + 1 == a.l);
       // ---- P1: t = [D+ M5op^-1] Dh_oe (D+ p) on O
       phase(a.sch[0], a.nsch[0], a.nbrO, true, a.linksO, sO, eg0,
             [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
-              Spinor<A> acc;
-              zero(acc);
-              simd_hop<P, LS, false>(acc, row, live, pin1, sB, NB, eg, s, lraw, ring, lane,
-                                     tid);
+              Spinor<A> acc[NSL];
+              simd_hop_out<P, LS, false>(acc, row, live, pin1, sB, NB, eg, w, lraw, ring, lane, tid);
               __syncthreads();   // the ring becomes the post buffer
-              to_buf(buf, acc, s, lane);
+#pragma unroll
+              for (int j = 0; j < NSL; j++) to_buf(buf, acc[j], w + j * LSP, lane);
               __syncthreads();
               post_recurrence<A, LS, false>(buf, K, tid, NT);
               __syncthreads();
-              from_buf(acc, buf, s, lane);
-              store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
+#pragma unroll
+              for (int j = 0; j < NSL; j++) {
+                from_buf(acc[j], buf, w + j * LSP, lane);
+                store_spinor<P>(a.t, sO, (long)pos * NB + eg, w + j * LSP, acc[j]);
+              }
             });
       if (!barrier()) return;
       // ---- P2: y = M5op p - 1/4 Dh_eo t on E; <p, A_s p> = ||y||^2 over the block
@@ -568,20 +662,23 @@ simd_local_kernel(const SimdArgs a) {
         const A hs = A(-0.25);
         phase(a.sch[1], a.nsch[1], a.nbrE, false, a.linksE, sE, eg0,
               [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
-                Spinor<A> acc;
-                zero(acc);
-                simd_hop<P, LS, false>(acc, row, live, a.t, sO, NB, eg, s, lraw, ring, lane,
-                                       tid);
-#pragma unroll
-                for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
+                Spinor<A> acc[NSL];
+                simd_hop_out<P, LS, false>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,
+                                           tid);
                 const long e = (long)pos * NB + eg;
-                if (pos < a.nBE) add_m5<P, false>(acc, a.p, sB, e, s, LS, K);
-                nrm += norm2(acc);
-                if (!last) store_spinor<P>(a.y, sE, e, s, acc);
+#pragma unroll
+                for (int j = 0; j < NSL; j++) {
+                  const int s = w + j * LSP;
+#pragma unroll
+                  for (int q = 0; q < 12; q++) acc[j].c[q] = cscale(hs, acc[j].c[q]);
+                  if (pos < a.nBE) add_m5<P, false>(acc[j], a.p, sB, e, s, LS, K);
+                  nrm += norm2(acc[j]);
+                  if (!last) store_spinor<P>(a.y, sE, e, s, acc[j]);
+                }
               });
-        write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
+        write_partial<A, LSP>(nrm, red, part + ci * 32, w, lane);
         if (!barrier()) return;
-        const double pap = slot_total(part, C, sc, s, lane);
+        const double pap = slot_total(part, C, sc, w, lane);
         alpha = (pap > 0.0 && isfinite(pap)) ? rho / pap : 0.0;
       }
       if (last) {
@@ -589,31 +686,38 @@ simd_local_kernel(const SimdArgs a) {
         const A al = A(alpha);
         for (int pos = ci; pos < a.nBE; pos += C) {
           const long e = (long)pos * NB + eg;
-          Spinor<A> xv, pv;
-          ld_spinor<P>(xv, a.x, sB, e, s);
-          ld_spinor<P>(pv, a.p, sB, e, s);
 #pragma unroll
-          for (int q = 0; q < 12; q++) {
-            xv.c[q].x += al * pv.c[q].x;
-            xv.c[q].y += al * pv.c[q].y;
+          for (int j = 0; j < NSL; j++) {
+            const int s = w + j * LSP;
+            Spinor<A> xv, pv;
+            ld_spinor<P>(xv, a.x, sB, e, s);
+            ld_spinor<P>(pv, a.p, sB, e, s);
+#pragma unroll
+            for (int q = 0; q < 12; q++) {
+              xv.c[q].x += al * pv.c[q].x;
+              xv.c[q].y += al * pv.c[q].y;
+            }
+            store_spinor<P>(a.x, sB, e, s, xv);
           }
-          store_spinor<P>(a.x, sB, e, s, xv);
         }
         break;
       }
       // ---- P3: s = [M5op^-dag D+^dag] Dh_oe^dag y on O
       phase(a.sch[2], a.nsch[2], a.nbrO, false, a.linksO, sO, eg0,
             [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
-              Spinor<A> acc;
-              zero(acc);
-              simd_hop<P, LS, true>(acc, row, live, a.y, sE, NB, eg, s, lraw, ring, lane, tid);
+              Spinor<A> acc[NSL];
+              simd_hop_out<P, LS, true>(acc, row, live, a.y, sE, NB, eg, w, lraw, ring, lane, tid);
               __syncthreads();
-              to_buf(buf, acc, s, lane);
+#pragma unroll
+              for (int j = 0; j < NSL; j++) to_buf(buf, acc[j], w + j * LSP, lane);
               __syncthreads();
               post_recurrence<A, LS, true>(buf, K, tid, NT);
               __syncthreads();
-              from_buf(acc, buf, s, lane);
-              store_spinor<P>(a.t, sO, (long)pos * NB + eg, s, acc);
+#pragma unroll
+              for (int j = 0; j < NSL; j++) {
+                from_buf(acc[j], buf, w + j * LSP, lane);
+                store_spinor<P>(a.t, sO, (long)pos * NB + eg, w + j * LSP, acc[j]);
+              }
             });
       if (!barrier()) return;
       // ---- P4: r -= alpha (M5op^dag y - 1/4 D+^dag Dh_eo^dag s) on BE; ||r||^2 -> beta
@@ -622,32 +726,35 @@ simd_local_kernel(const SimdArgs a) {
         const A al = A(alpha), hs = A(a.hs_b);
         phase(a.sch[3], a.nsch[3], a.nbrE, false, a.linksE, sE, eg0,
               [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
-                Spinor<A> acc;
-                zero(acc);
-                simd_hop<P, LS, true>(acc, row, live, a.t, sO, NB, eg, s, lraw, ring, lane,
-                                      tid);
+                Spinor<A> acc[NSL];
+                simd_hop_out<P, LS, true>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,
+                                          tid);
                 if (!a.trivial) {
                   __syncthreads();   // the ring becomes the slice-exchange buffer
-                  dplus_slices<A, LS, true>(acc, buf, K, s, lane);
+                  dplus_slices<A, LS, NSL, true>(acc, buf, K, w, lane);
                 }
-#pragma unroll
-                for (int q = 0; q < 12; q++) acc.c[q] = cscale(hs, acc.c[q]);
                 const long e = (long)pos * NB + eg;
-                add_m5<P, true>(acc, a.y, sE, e, s, LS, K);
-                Spinor<A> rr;
-                ld_spinor<P>(rr, a.r, sB, e, s);
 #pragma unroll
-                for (int q = 0; q < 12; q++) {
-                  rr.c[q].x -= al * acc.c[q].x;
-                  rr.c[q].y -= al * acc.c[q].y;
+                for (int j = 0; j < NSL; j++) {
+                  const int s = w + j * LSP;
+#pragma unroll
+                  for (int q = 0; q < 12; q++) acc[j].c[q] = cscale(hs, acc[j].c[q]);
+                  add_m5<P, true>(acc[j], a.y, sE, e, s, LS, K);
+                  Spinor<A> rr;
+                  ld_spinor<P>(rr, a.r, sB, e, s);
+#pragma unroll
+                  for (int q = 0; q < 12; q++) {
+                    rr.c[q].x -= al * acc[j].c[q].x;
+                    rr.c[q].y -= al * acc[j].c[q].y;
+                  }
+                  store_spinor<P>(a.r, sB, e, s, rr);
+                  round_to_storage<P>(rr);
+                  nrm += norm2(rr);
                 }
-                store_spinor<P>(a.r, sB, e, s, rr);
-                round_to_storage<P>(rr);
-                nrm += norm2(rr);
               });
-        write_partial<A, LS>(nrm, red, part + ci * 32, s, lane);
+        write_partial<A, LSP>(nrm, red, part + ci * 32, w, lane);
         if (!barrier()) return;
-        const double rr_new = slot_total(part, C, sc, s, lane);
+        const double rr_new = slot_total(part, C, sc, w, lane);
         beta = (rho > 0.0 && isfinite(rr_new)) ? rr_new / rho : 0.0;
         rho = rr_new;
       }
@@ -656,23 +763,29 @@ simd_local_kernel(const SimdArgs a) {
         const A al = A(alpha), be = A(beta);
         for (int pos = ci; pos < a.nBE; pos += C) {
           const long e = (long)pos * NB + eg;
-          Spinor<A> xv, pv, rv;
-          ld_spinor<P>(xv, a.x, sB, e, s);
-          ld_spinor<P>(pv, a.p, sB, e, s);
-          ld_spinor<P>(rv, a.r, sB, e, s);
+          Spinor<A> pv[NSL];
 #pragma unroll
-          for (int q = 0; q < 12; q++) {
-            xv.c[q].x += al * pv.c[q].x;
-            xv.c[q].y += al * pv.c[q].y;
-            pv.c[q].x = rv.c[q].x + be * pv.c[q].x;
-            pv.c[q].y = rv.c[q].y + be * pv.c[q].y;
+          for (int j = 0; j < NSL; j++) {
+            const int s = w + j * LSP;
+            Spinor<A> xv, rv;
+            ld_spinor<P>(xv, a.x, sB, e, s);
+            ld_spinor<P>(pv[j], a.p, sB, e, s);
+            ld_spinor<P>(rv, a.r, sB, e, s);
+#pragma unroll
+            for (int q = 0; q < 12; q++) {
+              xv.c[q].x += al * pv[j].c[q].x;
+              xv.c[q].y += al * pv[j].c[q].y;
+              pv[j].c[q].x = rv.c[q].x + be * pv[j].c[q].x;
+              pv[j].c[q].y = rv.c[q].y + be * pv[j].c[q].y;
+            }
+            store_spinor<P>(a.x, sB, e, s, xv);
+            store_spinor<P>(a.p, sB, e, s, pv[j]);
+            round_to_storage<P>(pv[j]);
           }
-          store_spinor<P>(a.x, sB, e, s, xv);
-          store_spinor<P>(a.p, sB, e, s, pv);
           if (!a.trivial) {
-            round_to_storage<P>(pv);
-            dplus_slices<A, LS, false>(pv, buf, K, s, lane);
-            store_spinor<P>(a.u, sB, e, s, pv);
+            dplus_slices<A, LS, NSL, false>(pv, buf, K, w, lane);
+#pragma unroll
+            for (int j = 0; j < NSL; j++) store_spinor<P>(a.u, sB, e, w + j * LSP, pv[j]);
           }
         }
       }

@@ -19,7 +19,7 @@ static cudaError_t launch_ls(const SimdArgs& a, int* grid_cap, int nsm, cudaStre
   if (e != cudaSuccess) return e;
   if (query) {
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * LS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * LS / simd_nsl<P>(), smem);
     if (e != cudaSuccess) return e;
     *grid_cap = per_sm * nsm;
     return cudaSuccess;
@@ -27,7 +27,7 @@ static cudaError_t launch_ls(const SimdArgs& a, int* grid_cap, int nsm, cudaStre
   SimdArgs b = a;
   void* args[] = {&b};
   return cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)(a.nslots * a.C)),
-                                     dim3(32, LS), args, smem, st);
+                                     dim3(32, LS / simd_nsl<P>()), args, smem, st);
 }
 
 template <>
