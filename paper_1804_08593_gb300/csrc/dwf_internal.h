@@ -91,6 +91,10 @@ struct SimdLocal {
   unsigned* ctr = nullptr;    // barrier counters
   double* partial = nullptr;
   int cap_slots = 0, cap_C = 0;
+  // launch-variant tuner per storage precision: -1 undecided; events of the timed calls
+  int tune_chosen[4] = {-1, -1, -1, -1};
+  int tune_next[4] = {0, 0, 0, 0};
+  cudaEvent_t tune_ev[4][12] = {};
   ~SimdLocal();
 };
 
@@ -266,7 +270,7 @@ dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const voi
                             int prec_outer, long Vp_outer, double num, const double* den,
                             const SimdFields& F);
 template <int P>
-cudaError_t simd_launch_p(const SimdArgs& a, int Ls, int* grid_cap, int nsm, cudaStream_t st,
+cudaError_t simd_launch_p(const SimdArgs& a, int Ls, int v, int* grid_cap, int nsm, cudaStream_t st,
                           bool query);
 
 // ---- vector kernels (blas.cu) ----

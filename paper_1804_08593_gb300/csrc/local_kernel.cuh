@@ -126,14 +126,14 @@ __host__ __device__ constexpr size_t simd_lraw_bytes() {
 template <int P>
 __host__ __device__ constexpr bool simd_ring() { return P != P64; }
 template <int P>
-__host__ __device__ constexpr size_t simd_region_bytes(int ls) {
-  const size_t ring = simd_ring<P>() ? (size_t)2 * Prec<P>::NCH * 32 * ls * 16 : 0;
+__host__ __device__ constexpr size_t simd_region_bytes(int ls, int rs) {
+  const size_t ring = simd_ring<P>() ? (size_t)rs * Prec<P>::NCH * 32 * ls * 16 : 0;
   const size_t buf = (size_t)ls * 24 * 32 * sizeof(typename Prec<P>::acc);
   return ring > buf ? ring : buf;
 }
 template <int P>
-__host__ __device__ constexpr size_t simd_smem_bytes(int ls) {
-  return 2 * simd_lraw_bytes<P>() + simd_region_bytes<P>(ls);
+__host__ __device__ constexpr size_t simd_smem_bytes(int ls, int rs) {
+  return 2 * simd_lraw_bytes<P>() + simd_region_bytes<P>(ls, rs);
 }
 
 // Copies the links of the live directions of the tile at element e0 into lraw (cp.async
@@ -270,7 +270,7 @@ __device__ __forceinline__ void simd_term_d(int d, HopAcc<P>& acc, const uint4* 
 // spinors go through a two-slot cp.async ring in shared memory, so the copy of the next live
 // direction is in flight while the current one is computed (each thread reads back only its
 // own copies: no block barrier).
-template <int P, int LS, bool DAG>
+template <int P, int LS, bool DAG, int RS>
 __device__ __forceinline__ void simd_hop(HopAcc<P>& acc, const uint32_t* row, uint32_t live,
                                          const void* in, long stride, int NB, long eg, int w,
                                          const uint4* lraw, uint4* ring, int lane, int tid) {
@@ -290,7 +290,8 @@ __device__ __forceinline__ void simd_hop(HopAcc<P>& acc, const uint32_t* row, ui
       simd_term_d<P, DAG>(d, acc, v, 1, 0, lraw, lane);
     }
   } else {
-    // ring slot layout: [slot][slice j][chunk k][thread]
+    // ring slot layout: [slot][slice j][chunk k][thread]; RS slots keep RS - 1 directions in
+    // flight ahead of the one being computed
     auto issue = [&](int d, int slot) {
       const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)w * NCH) * stride +
                        (long)__ldg(row + d) * NB + eg;
@@ -302,35 +303,37 @@ __device__ __forceinline__ void simd_hop(HopAcc<P>& acc, const uint32_t* row, ui
           cp_async16<false>(dst + (j * NCH + k) * NT, q + ((long)j * LSP * NCH + k) * stride);
       cp_async_commit();
     };
-    if (!live) return;
-    int slot = 0;
-    issue(__ffs(live) - 1, 0);
+    // the i-th live direction (i from 0): clear the i lowest set bits
+    auto nth = [&](int i) {
+      uint32_t m = live;
+      for (int k = 0; k < i; k++) m &= m - 1u;
+      return __ffs(m) - 1;
+    };
+    const int n = __popc(live);
 #pragma unroll
-    for (int d = 0; d < 8; d++) {
-      if (!((live >> d) & 1u)) continue;
-      const uint32_t later = live & ~((2u << d) - 1u);
-      if (later) {
-        issue(__ffs(later) - 1, slot ^ 1);
-        cp_async_wait<1>();
-      } else {
-        cp_async_wait<0>();
-      }
-      const uint4* q = ring + (slot * NSL * NCH) * NT + tid;
-      simd_term_d<P, DAG>(d, acc, q, NT, NCH * NT, lraw, lane);
-      slot ^= 1;
+    for (int i = 0; i < RS - 1; i++)
+      if (i < n) issue(nth(i), i);
+    for (int i = 0; i < n; i++) {
+      if (i + RS - 1 < n) issue(nth(i + RS - 1), (i + RS - 1) % RS);
+      const int newer = min(RS - 1, n - 1 - i);   // groups committed after direction i's
+      if (newer >= 2) cp_async_wait<2>();
+      else if (newer == 1) cp_async_wait<1>();
+      else cp_async_wait<0>();
+      const uint4* q = ring + ((i % RS) * NSL * NCH) * NT + tid;
+      simd_term_d<P, DAG>(nth(i), acc, q, NT, NCH * NT, lraw, lane);
     }
   }
 }
 
 // The hop of the tile, unpacked into one spinor per slice of the thread.
-template <int P, int LS, bool DAG>
+template <int P, int LS, bool DAG, int RS>
 __device__ __forceinline__ void simd_hop_out(Spinor<typename Prec<P>::acc> (&out)[simd_nsl<P>()],
                                              const uint32_t* row, uint32_t live, const void* in,
                                              long stride, int NB, long eg, int w,
                                              const uint4* lraw, uint4* ring, int lane, int tid) {
   HopAcc<P> h;
   hop_acc_zero<P>(h);
-  simd_hop<P, LS, DAG>(h, row, live, in, stride, NB, eg, w, lraw, ring, lane, tid);
+  simd_hop<P, LS, DAG, RS>(h, row, live, in, stride, NB, eg, w, lraw, ring, lane, tid);
   hop_acc_out<P, simd_nsl<P>()>(h, out);
 }
 
@@ -529,9 +532,16 @@ __device__ __forceinline__ double slot_total(const double* part, int C, double* 
   return t;
 }
 
-template <int P, int LS>
-__global__ void __launch_bounds__(32 * LS / simd_nsl<P>(), (P == P64) ? 1 : 2)
+// Launch variants (timed by the host's tuner): V = 0 two-slot ring, register budget for two
+// CTAs per SM; V = 1 three-slot ring (two directions in flight); V = 2 two-slot ring, budget
+// for three CTAs per SM.
+__host__ __device__ constexpr int simd_rs(int v) { return v == 1 ? 3 : 2; }
+__host__ __device__ constexpr int simd_minb(int p, int v) { return p == P64 ? 1 : v == 2 ? 3 : 2; }
+
+template <int P, int LS, int V>
+__global__ void __launch_bounds__(32 * LS / simd_nsl<P>(), simd_minb(P, V))
 simd_local_kernel(const SimdArgs a) {
+  constexpr int RS = simd_rs(V);
   using A = typename Prec<P>::acc;
   constexpr int NSL = simd_nsl<P>();
   constexpr int LSP = LS / NSL;    // warps; thread (lane, w) handles slices w + j LSP
@@ -642,7 +652,7 @@ simd_local_kernel(const SimdArgs a) {
       phase(a.sch[0], a.nsch[0], a.nbrO, true, a.linksO, sO, eg0,
             [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
               Spinor<A> acc[NSL];
-              simd_hop_out<P, LS, false>(acc, row, live, pin1, sB, NB, eg, w, lraw, ring, lane, tid);
+              simd_hop_out<P, LS, false, RS>(acc, row, live, pin1, sB, NB, eg, w, lraw, ring, lane, tid);
               __syncthreads();   // the ring becomes the post buffer
 #pragma unroll
               for (int j = 0; j < NSL; j++) to_buf(buf, acc[j], w + j * LSP, lane);
@@ -663,7 +673,7 @@ simd_local_kernel(const SimdArgs a) {
         phase(a.sch[1], a.nsch[1], a.nbrE, false, a.linksE, sE, eg0,
               [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
                 Spinor<A> acc[NSL];
-                simd_hop_out<P, LS, false>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,
+                simd_hop_out<P, LS, false, RS>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,
                                            tid);
                 const long e = (long)pos * NB + eg;
 #pragma unroll
@@ -706,7 +716,7 @@ simd_local_kernel(const SimdArgs a) {
       phase(a.sch[2], a.nsch[2], a.nbrO, false, a.linksO, sO, eg0,
             [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
               Spinor<A> acc[NSL];
-              simd_hop_out<P, LS, true>(acc, row, live, a.y, sE, NB, eg, w, lraw, ring, lane, tid);
+              simd_hop_out<P, LS, true, RS>(acc, row, live, a.y, sE, NB, eg, w, lraw, ring, lane, tid);
               __syncthreads();
 #pragma unroll
               for (int j = 0; j < NSL; j++) to_buf(buf, acc[j], w + j * LSP, lane);
@@ -727,7 +737,7 @@ simd_local_kernel(const SimdArgs a) {
         phase(a.sch[3], a.nsch[3], a.nbrE, false, a.linksE, sE, eg0,
               [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
                 Spinor<A> acc[NSL];
-                simd_hop_out<P, LS, true>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,
+                simd_hop_out<P, LS, true, RS>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,
                                           tid);
                 if (!a.trivial) {
                   __syncthreads();   // the ring becomes the slice-exchange buffer

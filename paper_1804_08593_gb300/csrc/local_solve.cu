@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <numeric>
 #include <vector>
 
@@ -27,6 +29,9 @@ SimdLocal::~SimdLocal() {
   }
   cudaFree(ctr);
   cudaFree(partial);
+  for (auto& row : tune_ev)
+    for (auto e : row)
+      if (e) cudaEventDestroy(e);
 }
 
 namespace {
@@ -259,14 +264,71 @@ static dwf_status ensure_simd_links(dwf_ctx* h, SimdLocal* S, int prec) {
   return DWF_OK;
 }
 
-static cudaError_t simd_launch(int prec, const SimdArgs& a, int Ls, int* cap, int nsm,
+static cudaError_t simd_launch(int prec, const SimdArgs& a, int Ls, int v, int* cap, int nsm,
                                cudaStream_t st, bool query) {
   switch (prec) {
-    case P64: return simd_launch_p<P64>(a, Ls, cap, nsm, st, query);
-    case P32: return simd_launch_p<P32>(a, Ls, cap, nsm, st, query);
-    case P16: return simd_launch_p<P16>(a, Ls, cap, nsm, st, query);
-    default: return simd_launch_p<PB16>(a, Ls, cap, nsm, st, query);
+    case P64: return simd_launch_p<P64>(a, Ls, v, cap, nsm, st, query);
+    case P32: return simd_launch_p<P32>(a, Ls, v, cap, nsm, st, query);
+    case P16: return simd_launch_p<P16>(a, Ls, v, cap, nsm, st, query);
+    default: return simd_launch_p<PB16>(a, Ls, v, cap, nsm, st, query);
   }
+}
+
+// Launch-variant tuner of the local-solve kernel (FP32/FP16/BF16 have three variants: ring
+// depth and register budget): the first calls per precision run every variant once untimed,
+// then twice timed with CUDA events on the stream; once all events have completed (checked
+// without blocking at later calls) the fastest is kept.  Calls under stream capture use the
+// current choice.  DWF_LOCAL_VARIANT=<v> forces variant v.
+constexpr int SIMD_NV = 3, SIMD_TUNE_ROUNDS = 2;
+
+static int simd_pick(SimdLocal* S, int prec, cudaStream_t st, bool capturing, int* timed) {
+  *timed = -1;
+  if (prec == P64) return 0;
+  if (const char* f = getenv("DWF_LOCAL_VARIANT")) {
+    const int v = atoi(f);
+    if (v >= 0 && v < SIMD_NV) return v;
+  }
+  int& chosen = S->tune_chosen[prec];
+  int& next = S->tune_next[prec];
+  const int nt = SIMD_TUNE_ROUNDS * SIMD_NV;
+  if (chosen >= 0) return chosen;
+  if (next >= SIMD_NV + nt) {   // every candidate timed: decide once the events are done
+    if (capturing) return 0;
+    bool done = true;
+    for (int i = 0; i < 2 * nt; i++)
+      done = done && cudaEventQuery(S->tune_ev[prec][i]) == cudaSuccess;
+    cudaGetLastError();
+    if (!done) return 0;
+    float best = 0.f, tv[SIMD_NV];
+    for (int v = 0; v < SIMD_NV; v++) {
+      float t = 0.f;
+      for (int i = v; i < nt; i += SIMD_NV) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, S->tune_ev[prec][2 * i], S->tune_ev[prec][2 * i + 1]);
+        t += ms;
+      }
+      tv[v] = t / SIMD_TUNE_ROUNDS;
+      if (chosen < 0 || t < best) {
+        best = t;
+        chosen = v;
+      }
+    }
+    if (getenv("DWF_TUNE_LOG"))
+      fprintf(stderr, "dwf tune local solve P%d: variant %d (%.3f / %.3f / %.3f ms)\n", prec,
+              chosen, tv[0], tv[1], tv[2]);
+    for (auto& e : S->tune_ev[prec]) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
+    return chosen;
+  }
+  if (capturing) return 0;
+  if (next == 0)
+    for (int i = 0; i < 2 * nt; i++) cudaEventCreate(&S->tune_ev[prec][i]);
+  const int v = next % SIMD_NV;
+  if (next >= SIMD_NV) *timed = next - SIMD_NV;
+  next++;
+  return v;
 }
 
 dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const void* r_outer,
@@ -317,7 +379,11 @@ dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const voi
   int dev = 0, nsm = 1, cap = 0;
   DWF_CUDA(cudaGetDevice(&dev));
   DWF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  DWF_CUDA(simd_launch(prec, a, h->Ls, &cap, nsm, h->stream, true));
+  cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(h->stream, &capst);
+  int timed = -1;
+  const int v = simd_pick(S, prec, h->stream, capst != cudaStreamCaptureStatusNone, &timed);
+  DWF_CUDA(simd_launch(prec, a, h->Ls, v, &cap, nsm, h->stream, true));
   if (cap < 1) return set_error(DWF_ERR_CUDA, "local-solve kernel cannot be resident");
   const int most = std::max(1, std::max(S->nE, S->nO) / 2);   // positions per CTA >= 2
   int C = std::max(1, std::min(cap / S->ngroups, most));
@@ -354,7 +420,9 @@ dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const voi
                                    : prec == PB16 ? "local_solve_bf16"
                                    : prec == P32 ? "local_solve_f32" : "local_solve_f64",
                it_bytes * l, 0.0);
-  DWF_CUDA(simd_launch(prec, a, h->Ls, &cap, nsm, h->stream, false));
+  if (timed >= 0) DWF_CUDA(cudaEventRecord(S->tune_ev[prec][2 * timed], h->stream));
+  DWF_CUDA(simd_launch(prec, a, h->Ls, v, &cap, nsm, h->stream, false));
+  if (timed >= 0) DWF_CUDA(cudaEventRecord(S->tune_ev[prec][2 * timed + 1], h->stream));
   return DWF_OK;
 }
 
