@@ -94,7 +94,7 @@ struct SimdLocal {
   // launch-variant tuner per storage precision: -1 undecided; events of the timed calls
   int tune_chosen[4] = {-1, -1, -1, -1};
   int tune_next[4] = {0, 0, 0, 0};
-  cudaEvent_t tune_ev[4][12] = {};
+  cudaEvent_t tune_ev[4][24] = {};
   ~SimdLocal();
 };
 

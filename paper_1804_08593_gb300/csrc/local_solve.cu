@@ -279,7 +279,7 @@ static cudaError_t simd_launch(int prec, const SimdArgs& a, int Ls, int v, int* 
 // then twice timed with CUDA events on the stream; once all events have completed (checked
 // without blocking at later calls) the fastest is kept.  Calls under stream capture use the
 // current choice.  DWF_LOCAL_VARIANT=<v> forces variant v.
-constexpr int SIMD_NV = 3, SIMD_TUNE_ROUNDS = 2;
+constexpr int SIMD_NV = 3, SIMD_TUNE_ROUNDS = 4;
 
 static int simd_pick(SimdLocal* S, int prec, cudaStream_t st, bool capturing, int* timed) {
   *timed = -1;
