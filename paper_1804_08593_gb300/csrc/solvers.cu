@@ -427,11 +427,15 @@ struct InnerVectors {
   int prec = 0;                // storage precision of the local solves
 };
 
-// Which local solver MSPCG uses: the persistent block-SIMD kernel (default) or one launch per
-// operator stage (DWF_LOCAL_SOLVER=stages), kept as a second implementation to compare with.
-static bool use_simd_local() {
+// Which local solver MSPCG uses: the persistent block-SIMD kernel or one launch per operator
+// stage.  Default: persistent for FP32/FP16/BF16 local solves; stages for FP64, where the
+// persistent kernel (one slice per thread, one CTA per SM at its register use) measured slower.
+// DWF_LOCAL_SOLVER=persistent|stages forces one.
+static bool use_simd_local(int inner) {
   const char* e = getenv("DWF_LOCAL_SOLVER");
-  return !(e && strcmp(e, "stages") == 0);
+  if (e && strcmp(e, "stages") == 0) return false;
+  if (e && strcmp(e, "persistent") == 0) return true;
+  return inner != P64;
 }
 
 static dwf_status precondition_stages(const OpEngine& Em, const OpEngine& Ei, const void* r,
@@ -562,7 +566,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   stats_init(stats);
   const Geom& g = layL->g;     // outer vectors
   const Geom& gb = lay->g;     // local solves
-  const bool simd = use_simd_local();
+  const bool simd = use_simd_local(inner);
   long max_ctas = std::max(g.Vp, gb.Vp) / 32;
   if (exact && !simd) {
     // before the engines pack links: packing also gathers the halo copies

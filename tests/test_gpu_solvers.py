@@ -114,8 +114,7 @@ def test_cg_failure_modes():
 
 @pytest.mark.parametrize("solver", ["persistent", "stages"])
 def test_mspcg_fp64_matches_oracle(solver, monkeypatch):
-    if solver == "stages":
-        monkeypatch.setenv("DWF_LOCAL_SOLVER", "stages")
+    monkeypatch.setenv("DWF_LOCAL_SOLVER", solver)
     dwf = lib()
     p, U, phi, xo, ko, hist = small_ms()
     h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
@@ -184,8 +183,7 @@ def exact_case():
 
 @pytest.mark.parametrize("solver", ["persistent", "stages"])
 def test_mspcg_exact_blocks_fp64_matches_oracle(solver, monkeypatch):
-    if solver == "stages":
-        monkeypatch.setenv("DWF_LOCAL_SOLVER", "stages")
+    monkeypatch.setenv("DWF_LOCAL_SOLVER", solver)
     dwf = lib()
     p, U, phi, xo, ko, hist = exact_case()
     h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U))
@@ -282,8 +280,7 @@ def multi_tile_oracle(name):
 @pytest.mark.parametrize("name", sorted(MULTI_TILE))
 def test_mspcg_exact_multi_tile_blocks_follow_oracle(name, solver, monkeypatch):
     """Both local-solve implementations (one persistent launch; one launch per stage)."""
-    if solver == "stages":
-        monkeypatch.setenv("DWF_LOCAL_SOLVER", "stages")
+    monkeypatch.setenv("DWF_LOCAL_SOLVER", solver)
     dwf = lib()
     p, U, phi, blk, l, n = multi_tile(name)
     xo, ko, hist = multi_tile_oracle(name)
