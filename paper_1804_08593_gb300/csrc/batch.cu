@@ -3,15 +3,17 @@
 //
 // Problems with the same Ls share one concatenated site space (each problem padded to whole
 // 32-site tiles); every problem is one reduction/scalar segment with its own fifth-dimension
-// matrices, M5op coefficients, stop flag and CG scalars.  One CG step of every problem of a
-// group is five launches (stages A, B, A^dag, B^dag and the update); the stage launches are
-// persistent (a grid of a few CTAs per SM looping over every problem's tiles) with the grid
-// size picked by a small autotuner, and a chunk of steps of all groups is captured once in a
-// CUDA graph and replayed.  FP32 CG with FP64 reliable updates per problem (the true
-// residual is recomputed in FP64 when a problem's FP32 residual has dropped by delta = 0.1,
-// or at convergence).
+// matrices, M5op coefficients, stop flag and CG scalars.  A chunk of 16 FP32 CG steps of every
+// problem of a group is one persistent, cooperative launch (batch_steps.cu: five phases per
+// step over all tiles, grid barriers with bounded waits); the grid size and the stages' link
+// staging are picked by timing the first chunks, and the chosen launches of all groups are
+// then captured once in a CUDA graph and replayed.  FP32 CG with FP64 reliable updates per
+// problem (the true residual is recomputed in FP64 when a problem's FP32 residual has dropped
+// by delta = 0.1, or at convergence), between replays.
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -53,6 +55,9 @@ struct Group {
   unsigned* counter = nullptr; // [nseg]
   double* partial = nullptr;   // [ntiles]
   int grid = 0;                // autotuned persistent grid of the stage launches
+  int sgrid = 0, sgather = 0;  // persistent CG-step launch: grid, link staging (tuned)
+  unsigned* bar = nullptr;     // barrier counter of the persistent launch
+  int* err = nullptr;          // set when a bounded device wait gives up
   int post_struct = 1;         // every problem has |beta/alpha| < 1: post by recurrences
   std::vector<void*> owned;
   ~Group() {
@@ -165,6 +170,7 @@ struct Batch {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   double* staged_links = nullptr;
+  unsigned long long wait_ns = 0;   // bounded device waits (DWF_WAIT_LIMIT_US; 0: default)
   std::vector<void*> owned;
   ~Batch() {
     if (st) cudaStreamSynchronize(st);
@@ -345,6 +351,90 @@ dwf_status g_cg_step(const Group& G, cudaStream_t st) {
   return DWF_OK;
 }
 
+// The launches of one CG step (as g_cg_step issues them) as arguments of the persistent
+// kernel that runs `nsteps` steps in one launch.
+void g_step_args(const Group& G, int nsteps, unsigned long long wait_ns, BatchStepArgs& b) {
+  const int* stop = G.fl + FL_STOP * G.nseg;
+  void** v = const_cast<void**>(G.f32);   // x, p, r, u, t, y, s
+  b = BatchStepArgs{};
+  StageArgs a = gbase(G, P32, 1, stop);
+  a.in = v[3];
+  a.out = v[4];
+  a.post = G.mats[1];
+  a.post_which = 0;
+  a.post_struct = 1;
+  a.post_pre = 1.0;
+  StageArgs bb = gbase(G, P32, 0, stop);
+  bb.in = v[4];
+  bb.out = v[5];
+  bb.in2 = v[1];
+  bb.local_mode = LOC_M5;
+  bb.hop_scale = -0.25;
+  bb.epi = EPI_NORM;
+  bb.red = gred(G, FIN_ALPHA);
+  bb.red.res = G.sc + SC_PAP * G.nseg;
+  bb.red.rho = G.sc + SC_RHO * G.nseg;
+  bb.red.alpha = G.sc + SC_ALPHA * G.nseg;
+  StageArgs ad = gbase(G, P32, 1, stop);
+  ad.in = v[5];
+  ad.out = v[6];
+  ad.post = G.mats[1];
+  ad.post_which = 1;
+  ad.post_struct = 1;
+  ad.post_pre = 1.0;
+  StageArgs bd = gbase(G, P32, 0, stop);
+  bd.in = v[6];
+  bd.in2 = v[5];
+  bd.local_mode = LOC_M5DAG;
+  bd.hop_scale = -0.25;
+  bd.post = G.mats[1];
+  bd.post_which = 2;
+  bd.post_sparse = 1;
+  bd.epi = EPI_CG_R;
+  bd.r = v[2];
+  bd.alpha = G.sc + SC_ALPHA * G.nseg;
+  bd.red = gred(G, FIN_BETA);
+  bd.red.rho = G.sc + SC_RHO * G.nseg;
+  bd.red.beta = G.sc + SC_BETA * G.nseg;
+  bd.red.stop2 = G.sc + SC_STOP2 * G.nseg;
+  bd.red.conv = G.fl + FL_CONV * G.nseg;
+  StageArgs* st4[4] = {&a, &bb, &ad, &bd};
+  for (StageArgs* x : st4) {
+    x->err = G.err;
+    x->wait_ns = wait_ns;
+    x->grid = 0;
+    finish_stage_args(*x, G.Ls);
+  }
+  b.A = a;
+  b.B = bb;
+  b.Ad = ad;
+  b.Bd = bd;
+  VecArgs& u = b.U;
+  u.x = v[0];
+  u.p = v[1];
+  u.r = v[2];
+  u.u = v[3];
+  u.Vp = G.Vp;
+  u.Vhb = (int)G.Vp;
+  u.Vhb_pad = (int)G.Vp;
+  u.alpha = G.sc + SC_ALPHA * G.nseg;
+  u.beta = G.sc + SC_BETA * G.nseg;
+  u.seg_cps = (int)G.ntiles;
+  u.do_x = u.do_p = u.do_u = 1;
+  u.stop = stop;
+  u.red.counter = G.counter;
+  u.stop_out = G.fl + FL_STOP * G.nseg;
+  u.conv_in = G.fl + FL_CONV * G.nseg;
+  u.iter = G.fl + FL_ITER * G.nseg;
+  u.tile_seg = G.tile_seg;
+  u.segp = G.segp[1];
+  b.ntiles = G.ntiles;
+  b.nsteps = nsteps;
+  b.bar = G.bar;
+  b.wait_ns = wait_ns;
+  b.err = G.err;
+}
+
 // r64 = b - A64 x64 for the problems with skip == 0; ||r64||^2 -> rr64.
 dwf_status g_true_residual(const Group& G, cudaStream_t st) {
   const int* skip = G.fl + FL_SKIP * G.nseg;
@@ -517,6 +607,9 @@ dwf_status build_group(Batch& B, Group& G, const dwf_problem* pr) {
   DWF_TRY(G.alloc(&G.fl, FL_N * G.nseg * sizeof(int)));
   DWF_TRY(G.alloc(&G.counter, G.nseg * sizeof(unsigned)));
   DWF_TRY(G.alloc(&G.partial, (size_t)G.ntiles * sizeof(double)));
+  DWF_TRY(G.alloc(&G.bar, sizeof(unsigned)));
+  DWF_TRY(G.alloc(&G.err, sizeof(int)));
+  DWF_CUDA(cudaMemsetAsync(G.err, 0, sizeof(int), st));
   DWF_CUDA(cudaMemsetAsync(G.sc, 0, SC_N * G.nseg * sizeof(double), st));
   DWF_CUDA(cudaMemsetAsync(G.fl, 0, FL_N * G.nseg * sizeof(int), st));
   DWF_CUDA(cudaMemsetAsync(G.counter, 0, G.nseg * sizeof(unsigned), st));
@@ -714,30 +807,129 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
   }
   DWF_CUDA(cudaStreamSynchronize(B.st));
 
-  // one chunk of CG steps of every group, captured once and replayed
+  // a chunk of CG steps of every group: one persistent launch per group.  The first chunks
+  // time the candidate launches (grid of 1 or 2 CTAs per SM or the largest co-resident grid,
+  // links read directly or staged by TMA bulk copies); the fastest of each group is then
+  // captured once in a CUDA graph and replayed.  Groups whose fifth-dimension post cannot use
+  // the recurrences keep one launch per stage (a captured chunk of g_cg_step).
   const int chunk = 16;
+  int dev = 0, nsm = 1;
+  DWF_CUDA(cudaGetDevice(&dev));
+  DWF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  if (const char* wl = getenv("DWF_WAIT_LIMIT_US")) {
+    const double us = atof(wl);
+    if (us >= 1.0 && us <= 1e7) B.wait_ns = (unsigned long long)(us * 1000.0);
+  }
+  const unsigned long long wait_ns = B.wait_ns;
+  struct Cand {
+    int gather, grid;
+  };
+  std::vector<std::vector<Cand>> cands(B.groups.size());
+  for (size_t gi = 0; gi < B.groups.size(); gi++) {
+    Group& G = *B.groups[gi];
+    if (!G.post_struct) continue;
+    BatchStepArgs ba;
+    g_step_args(G, chunk, wait_ns, ba);
+    for (int gather : {G_REG, G_TMA}) {
+      int cap = 0;
+      DWF_CUDA(batch_steps_launch(ba, G.Ls, gather, 0, &cap, nsm, B.st, true));
+      std::vector<int> grids;
+      for (int per : {1, 2}) if (per * nsm <= cap) grids.push_back(per * nsm);
+      if (cap > 2 * nsm) grids.push_back(cap);
+      for (int g : grids) cands[gi].push_back({gather, (int)std::min<long>(g, G.ntiles)});
+    }
+    if (cands[gi].empty()) G.post_struct = 0;   // cannot be resident: stage launches
+  }
+  size_t ntune = 0;
+  for (auto& c : cands) ntune = std::max(ntune, c.size());
+  std::vector<std::vector<float>> tuned(B.groups.size());
+  cudaEvent_t tev[2];
+  DWF_CUDA(cudaEventCreate(&tev[0]));
+  DWF_CUDA(cudaEventCreate(&tev[1]));
+  auto launch_chunk = [&](Group& G, int gather, int grid) -> dwf_status {
+    BatchStepArgs ba;
+    g_step_args(G, chunk, wait_ns, ba);
+    DWF_CUDA(cudaMemsetAsync(G.bar, 0, sizeof(unsigned), B.st));
+    int cap = 0;
+    DWF_CUDA(batch_steps_launch(ba, G.Ls, gather, grid, &cap, nsm, B.st, false));
+    return DWF_OK;
+  };
+  auto stage_chunk = [&](Group& G) -> dwf_status {
+    for (int k = 0; k < chunk; k++) DWF_TRY(g_cg_step(G, B.st));
+    return DWF_OK;
+  };
+  size_t tune_round = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  // a first un-captured step sets the kernels' attributes
-  for (auto& G : B.groups) DWF_TRY(g_cg_step(*G, B.st));
-  DWF_CUDA(cudaStreamSynchronize(B.st));
-  DWF_CUDA(cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < chunk; k++)
-    for (auto& G : B.groups) {
-      dwf_status s = g_cg_step(*G, B.st);
+  // a first un-captured step of the stage path sets its kernels' attributes
+  for (auto& G : B.groups)
+    if (!G->post_struct) DWF_TRY(g_cg_step(*G, B.st));
+  auto capture = [&]() -> dwf_status {
+    DWF_CUDA(cudaStreamSynchronize(B.st));
+    DWF_CUDA(cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal));
+    for (auto& Gp : B.groups) {
+      Group& G = *Gp;
+      dwf_status s = G.post_struct ? launch_chunk(G, G.sgather, G.sgrid) : stage_chunk(G);
       if (s != DWF_OK) {
         cudaStreamEndCapture(B.st, &graph);
         if (graph) cudaGraphDestroy(graph);
+        graph = nullptr;
         return s;
       }
     }
-  DWF_CUDA(cudaStreamEndCapture(B.st, &graph));
-  DWF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    DWF_CUDA(cudaStreamEndCapture(B.st, &graph));
+    DWF_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    return DWF_OK;
+  };
+  if (ntune == 0) DWF_TRY(capture());
+  // one chunk of every group: a tuning round (timed launches of the next candidate) or the
+  // captured graph
+  auto run_chunk = [&]() -> dwf_status {
+    if (tune_round >= ntune) {
+      DWF_CUDA(cudaGraphLaunch(exec, B.st));
+      return DWF_OK;
+    }
+    for (size_t gi = 0; gi < B.groups.size(); gi++) {
+      Group& G = *B.groups[gi];
+      if (!G.post_struct) {
+        DWF_TRY(stage_chunk(G));
+        continue;
+      }
+      const Cand& c = cands[gi][std::min(tune_round, cands[gi].size() - 1)];
+      DWF_CUDA(cudaEventRecord(tev[0], B.st));
+      DWF_TRY(launch_chunk(G, c.gather, c.grid));
+      DWF_CUDA(cudaEventRecord(tev[1], B.st));
+      DWF_CUDA(cudaEventSynchronize(tev[1]));
+      float ms = 0.f;
+      DWF_CUDA(cudaEventElapsedTime(&ms, tev[0], tev[1]));
+      if (tune_round < cands[gi].size()) tuned[gi].push_back(ms);
+    }
+    if (++tune_round == ntune) {
+      for (size_t gi = 0; gi < B.groups.size(); gi++) {
+        Group& G = *B.groups[gi];
+        if (!G.post_struct) continue;
+        size_t best = 0;
+        for (size_t k = 1; k < tuned[gi].size(); k++)
+          if (tuned[gi][k] < tuned[gi][best]) best = k;
+        G.sgather = cands[gi][best].gather;
+        G.sgrid = cands[gi][best].grid;
+        if (getenv("DWF_TUNE_LOG")) {
+          fprintf(stderr, "dwf tune batch Ls%d tiles %ld:", G.Ls, G.ntiles);
+          for (size_t k = 0; k < tuned[gi].size(); k++)
+            fprintf(stderr, " %s[gather%d grid%d %.2fms]", k == best ? "*" : "",
+                    cands[gi][k].gather, cands[gi][k].grid, tuned[gi][k]);
+          fprintf(stderr, "\n");
+        }
+      }
+      DWF_TRY(capture());
+    }
+    return DWF_OK;
+  };
 
-  int total_steps = 1;
+  int total_steps = 0;
   dwf_status status = DWF_OK;
   while (true) {
-    DWF_CUDA(cudaGraphLaunch(exec, B.st));
+    DWF_TRY(run_chunk());
     total_steps += chunk;
     bool all_done = true, any_ru = false;
     for (size_t gi = 0; gi < B.groups.size(); gi++) {
@@ -798,8 +990,16 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
     (void)any_ru;
     if (all_done) break;
   }
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  cudaEventDestroy(tev[0]);
+  cudaEventDestroy(tev[1]);
+  for (auto& Gp : B.groups) {   // a bounded device wait that gave up invalidates the solve
+    int e = 0;
+    DWF_CUDA(cudaMemcpyAsync(&e, Gp->err, sizeof(int), cudaMemcpyDeviceToHost, B.st));
+    DWF_CUDA(cudaStreamSynchronize(B.st));
+    if (e) return set_error(DWF_ERR_TIMEOUT, "batched solver: a bounded device wait gave up");
+  }
   // solutions out
   for (size_t gi = 0; gi < B.groups.size(); gi++) {
     Group& G = *B.groups[gi];

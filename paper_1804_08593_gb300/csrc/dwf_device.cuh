@@ -102,7 +102,15 @@ __device__ __forceinline__ uint32_t f2h(float a, float b, bool bf) {
   return r;
 }
 
-template <int P>
+// Read-only load of a field: through the non-coherent path (the field is not written during
+// the kernel), or with COH through L2 only (a persistent kernel that reads, after a grid
+// barrier, data other CTAs wrote earlier in the same launch).
+template <bool COH, typename T>
+__device__ __forceinline__ T ldf(const T* p) {
+  if constexpr (COH) return __ldcg(p); else return __ldg(p);
+}
+
+template <int P, bool COH = false>
 __device__ __forceinline__ void load_spinor(Spinor<typename Prec<P>::acc>& out, const void* base,
                                             long Vp, long site, int s) {
   constexpr int NCH = Prec<P>::NCH;
@@ -110,13 +118,13 @@ __device__ __forceinline__ void load_spinor(Spinor<typename Prec<P>::acc>& out, 
   if constexpr (P == P64) {
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      double2 v = __ldg(reinterpret_cast<const double2*>(p + k * Vp));
+      double2 v = ldf<COH>(reinterpret_cast<const double2*>(p + k * Vp));
       out.c[k] = {v.x, v.y};
     }
   } else if constexpr (P == P32) {
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-      float4 v = __ldg(reinterpret_cast<const float4*>(p + k * Vp));
+      float4 v = ldf<COH>(reinterpret_cast<const float4*>(p + k * Vp));
       out.c[2 * k] = {v.x, v.y};
       out.c[2 * k + 1] = {v.z, v.w};
     }
@@ -124,7 +132,7 @@ __device__ __forceinline__ void load_spinor(Spinor<typename Prec<P>::acc>& out, 
     constexpr bool BF = (P == PB16);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = __ldg(p + k * Vp);
+      uint4 v = ldf<COH>(p + k * Vp);
       float2 a = h2f(v.x, BF), b = h2f(v.y, BF), c = h2f(v.z, BF), d = h2f(v.w, BF);
       out.c[4 * k] = {a.x, a.y};
       out.c[4 * k + 1] = {b.x, b.y};

@@ -306,6 +306,24 @@ struct VecArgs {
 };
 cudaError_t launch_vec(int prec, const VecArgs& a, int Ls, cudaStream_t st);
 
+// ---- batched CG steps in one persistent launch (batch_steps.cu) ----
+// A, B, Ad, Bd: the four stage launches of a CG step on A = Mpc^dag Mpc (finished with
+// finish_stage_args), U: the update; nsteps steps per launch; bar: barrier counter, zero at
+// launch.
+struct BatchStepArgs {
+  StageArgs A, B, Ad, Bd;
+  VecArgs U;
+  long ntiles;
+  int nsteps;
+  unsigned* bar;
+  unsigned long long wait_ns;
+  int* err;
+};
+// query: *cap = the largest co-resident grid; otherwise a cooperative launch of `grid` CTAs.
+// gather: G_REG or G_TMA (how the stages read their links).
+cudaError_t batch_steps_launch(const BatchStepArgs& b, int Ls, int gather, int grid, int* cap,
+                               int nsm, cudaStream_t st, bool query);
+
 // Elementwise conversion out = in * f (f = sqrt(num / *den) if den else num), both fields of
 // the same geometry, with an optional reduction of <dotv, out> (dotv in out's precision).
 struct CastArgs {

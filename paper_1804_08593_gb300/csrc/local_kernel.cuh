@@ -36,6 +36,7 @@
 
 #include "dwf_device.cuh"
 #include "stage.cuh"
+#include "sync.cuh"
 #include "tc_m5.cuh"
 
 namespace dwf {
@@ -471,38 +472,6 @@ __device__ __forceinline__ A norm2(const Spinor<A>& v) {
 #pragma unroll
   for (int k = 0; k < 12; k++) n = fma(v.c[k].x, v.c[k].x, fma(v.c[k].y, v.c[k].y, n));
   return n;
-}
-
-// Barrier of the C CTAs of one slot: the counter counts arrivals; `target` is the number of
-// arrivals that completes this barrier.  Bounded: gives up after the wait limit, records the
-// error and returns false in every thread of the CTA (which then leaves the kernel; the
-// others then give up at their next barrier, so the launch always ends).
-__device__ __forceinline__ bool slot_barrier(unsigned* ctr, unsigned target,
-                                             unsigned long long wait_ns, int* err) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    __threadfence();
-    atomicAdd(ctr, 1u);
-    int ok = 1;
-    const unsigned long long lim = wait_ns ? wait_ns : tc::DEFAULT_WAIT_NS;
-    const unsigned long long t0 = tc::globaltimer_ns();
-    while (true) {
-      unsigned v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
-      if (v >= target) break;
-      if (tc::globaltimer_ns() - t0 > lim) {
-        ok = 0;
-        if (err) atomicExch(err, 1);
-        break;
-      }
-      __nanosleep(32);
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
 }
 
 // One FP64 partial per (CTA, lane) of the thread-level values v (summed over the warps).

@@ -243,7 +243,7 @@ __device__ __forceinline__ bool nbr_source(const StageArgs& a, uint32_t nb, cons
 }
 
 // LSM: links from the tile's shared-memory copy lsm ([dir][chunk][32]; lsite = lane)
-template <int P, int D, bool DAG, bool BLOCKED, bool LSM = false>
+template <int P, int D, bool DAG, bool BLOCKED, bool LSM = false, bool COH = false>
 __device__ __forceinline__ void hop_dir_nb(Spinor<typename Prec<P>::acc>& acc,
                                            const StageArgs& a, uint32_t nb, long lsite, int s,
                                            const void* lsm = nullptr) {
@@ -259,22 +259,22 @@ __device__ __forceinline__ void hop_dir_nb(Spinor<typename Prec<P>::acc>& acc,
   const long vl = LSM ? 32 : a.Vp_link;
   if constexpr (P == P16 || P == PB16) {
     const uint4* p = reinterpret_cast<const uint4*>(src) + ((long)s * 3) * vs + j;
-    const uint4 q[3] = {__ldg(p), __ldg(p + vs), __ldg(p + 2 * vs)};
+    const uint4 q[3] = {ldf<COH>(p), ldf<COH>(p + vs), ldf<COH>(p + 2 * vs)};
     const uint4* lp = reinterpret_cast<const uint4*>(lb) + (long)D * 3 * vl + lsite;
     hop_term16<P, D / 2, LSM>(acc, q, lp, vl, sgn);
   } else {
     Spinor<A> psi;
-    load_spinor<P>(psi, src, vs, j, s);
+    load_spinor<P, COH>(psi, src, vs, j, s);
     hop_term<P, D / 2, LSM>(acc, psi, lb, vl, lsite, D, sgn);
   }
 }
 
-template <int P, int D, bool DAG, bool BLOCKED, bool LSM = false>
+template <int P, int D, bool DAG, bool BLOCKED, bool LSM = false, bool COH = false>
 __device__ __forceinline__ void hop_dir(Spinor<typename Prec<P>::acc>& acc, const StageArgs& a,
                                         long site, long lsite, int s,
                                         const void* lsm = nullptr) {
-  hop_dir_nb<P, D, DAG, BLOCKED, LSM>(acc, a, __ldg(a.nbr + (long)D * a.Vp + site), lsite, s,
-                                      lsm);
+  hop_dir_nb<P, D, DAG, BLOCKED, LSM, COH>(acc, a, __ldg(a.nbr + (long)D * a.Vp + site), lsite,
+                                           s, lsm);
 }
 
 // FP32 and 16-bit stages: the eight neighbour spinors are gathered with cp.async into a
@@ -515,7 +515,7 @@ __host__ __device__ constexpr size_t tma_link_offset(int Ls, int post, int gathe
 //       4 = D+ M5op^-1 (dag: M5op^-dag D+^dag) by an O(Ls) recurrence per column
 // One direction of the paired-slice hop: neighbour spinors of slices w and w + lsp, the link
 // (from the tile's shared-memory copy) loaded once for both.
-template <int P, int D, bool DAG, bool BLOCKED>
+template <int P, int D, bool DAG, bool BLOCKED, bool COH = false>
 __device__ __forceinline__ void hop_pair_d(Spinor<typename Prec<P>::acc> (&acc)[2],
                                            const StageArgs& a, long site, int lane, int w,
                                            int lsp, const uint4* lsm) {
@@ -528,26 +528,26 @@ __device__ __forceinline__ void hop_pair_d(Spinor<typename Prec<P>::acc> (&acc)[
   constexpr bool back = (D & 1) != 0;
   const A sgn = (back != DAG) ? A(1) : A(-1);
   Spinor<A> psi0, psi1;
-  load_spinor<P>(psi0, src, vs, j, w);
-  load_spinor<P>(psi1, src, vs, j, w + lsp);
+  load_spinor<P, COH>(psi0, src, vs, j, w);
+  load_spinor<P, COH>(psi1, src, vs, j, w + lsp);
   cx<A> u[9];
   load_link9<P, true>(u, lsm, 32, lane, D);
   hop_term_u<P, D / 2>(acc[0], psi0, u, sgn);
   hop_term_u<P, D / 2>(acc[1], psi1, u, sgn);
 }
 
-template <int P, bool DAG, bool BLOCKED>
+template <int P, bool DAG, bool BLOCKED, bool COH = false>
 __device__ __forceinline__ void hop_pair(Spinor<typename Prec<P>::acc> (&acc)[2],
                                          const StageArgs& a, long site, int lane, int w,
                                          int lsp, const uint4* lsm) {
-  hop_pair_d<P, 0, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
-  hop_pair_d<P, 1, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
-  hop_pair_d<P, 2, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
-  hop_pair_d<P, 3, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
-  hop_pair_d<P, 4, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
-  hop_pair_d<P, 5, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
-  hop_pair_d<P, 6, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
-  hop_pair_d<P, 7, DAG, BLOCKED>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 0, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 1, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 2, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 3, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 4, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 5, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 6, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
+  hop_pair_d<P, 7, DAG, BLOCKED, COH>(acc, a, site, lane, w, lsp, lsm);
 }
 
 // Packed paired-slice hop (FP32): component k of slices w and w + lsp shares one float2, so
@@ -677,7 +677,7 @@ __device__ __forceinline__ void hop_pair_f2(Spinor<float> (&out)[2], const Stage
 // SP: slice mode (enum SliceMode).  In the paired modes thread (lane, w) computes slices w and
 // w + Ls/2 and loads each link once for both.
 // Returns false (uniformly over the CTA) when a bounded wait gave up: the caller stops.
-template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G, int SP = 1>
+template <int P, int LS, bool DAG, bool BLOCKED, int POST, int G, int SP = 1, bool COH = false>
 __device__ __forceinline__ bool stage_tile(const StageArgs& a, long tile,
                                            unsigned char* smem_raw, double* red_scratch,
                                            uint64_t* tc_mbar, uint32_t* tc_slot,
@@ -756,27 +756,27 @@ __device__ __forceinline__ bool stage_tile(const StageArgs& a, long tile,
       __syncthreads();
     } else if (G == G_TMA) {
       if (valid) {
-        hop_dir<P, 0, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
-        hop_dir<P, 1, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
-        hop_dir<P, 2, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
-        hop_dir<P, 3, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
-        hop_dir<P, 4, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
-        hop_dir<P, 5, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
-        hop_dir<P, 6, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
-        hop_dir<P, 7, DAG, BLOCKED, true>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 0, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 1, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 2, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 3, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 4, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 5, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 6, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
+        hop_dir<P, 7, DAG, BLOCKED, true, COH>(acc[0], a, site, lane, s, lsm);
       }
     } else {
       if constexpr (bpf_what(G) > 0) prefetch_tile<P, LS, BLOCKED, bpf_what(G)>(a, tile);
       if (valid) {
         const long lsite = site;
-        hop_dir<P, 0, DAG, BLOCKED>(acc[0], a, site, lsite, s);
-        hop_dir<P, 1, DAG, BLOCKED>(acc[0], a, site, lsite, s);
-        hop_dir<P, 2, DAG, BLOCKED>(acc[0], a, site, lsite, s);
-        hop_dir<P, 3, DAG, BLOCKED>(acc[0], a, site, lsite, s);
-        hop_dir<P, 4, DAG, BLOCKED>(acc[0], a, site, lsite, s);
-        hop_dir<P, 5, DAG, BLOCKED>(acc[0], a, site, lsite, s);
-        hop_dir<P, 6, DAG, BLOCKED>(acc[0], a, site, lsite, s);
-        hop_dir<P, 7, DAG, BLOCKED>(acc[0], a, site, lsite, s);
+        hop_dir<P, 0, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
+        hop_dir<P, 1, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
+        hop_dir<P, 2, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
+        hop_dir<P, 3, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
+        hop_dir<P, 4, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
+        hop_dir<P, 5, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
+        hop_dir<P, 6, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
+        hop_dir<P, 7, DAG, BLOCKED, false, COH>(acc[0], a, site, lsite, s);
       }
     }
   } else {
@@ -784,7 +784,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs& a, long tile,
     static_assert(gather_tma(G), "paired slices read the links from shared memory");
     static_assert(SP != SP_PAIR_F2 || P == P32, "packed pairs are FP32 only");
     if (valid) {
-      if constexpr (SP == SP_PAIR) hop_pair<P, DAG, BLOCKED>(acc, a, site, lane, w, LSP, lsm);
+      if constexpr (SP == SP_PAIR) hop_pair<P, DAG, BLOCKED, COH>(acc, a, site, lane, w, LSP, lsm);
       if constexpr (SP == SP_PAIR_F2) hop_pair_f2<DAG, BLOCKED>(acc, a, site, lane, w, LSP, lsm);
     }
   }
@@ -954,9 +954,9 @@ __device__ __forceinline__ bool stage_tile(const StageArgs& a, long tile,
       // M5op^dag x at s = alpha x_s + beta (P+ x_{s+1} + P- x_{s-1});
       // x_{Ls} = -mf x_0, x_{-1} = -mf x_{Ls-1}.
       Spinor<A> x0, xu, xd;
-      load_spinor<P>(x0, a.in2, a.Vp, site, s);
-      load_spinor<P>(xu, a.in2, a.Vp, site, s + 1 < LS ? s + 1 : 0);
-      load_spinor<P>(xd, a.in2, a.Vp, site, s > 0 ? s - 1 : LS - 1);
+      load_spinor<P, COH>(x0, a.in2, a.Vp, site, s);
+      load_spinor<P, COH>(xu, a.in2, a.Vp, site, s + 1 < LS ? s + 1 : 0);
+      load_spinor<P, COH>(xd, a.in2, a.Vp, site, s > 0 ? s - 1 : LS - 1);
       const Coef5<A> C = K5();
       const A fu = (s + 1 < LS) ? A(1) : -C.mf;
       const A fd = (s > 0) ? A(1) : -C.mf;
@@ -975,7 +975,7 @@ __device__ __forceinline__ bool stage_tile(const StageArgs& a, long tile,
     if (a.epi == EPI_CG_R) {
       const A al = A(a.alpha[seg]);
       Spinor<A> rr;
-      load_spinor<P>(rr, a.r, a.Vp, site, s);
+      load_spinor<P, COH>(rr, a.r, a.Vp, site, s);
   #pragma unroll
       for (int k = 0; k < 12; k++) {
         rr.c[k].x -= al * acc_j.c[k].x;
