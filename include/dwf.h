@@ -181,13 +181,16 @@ typedef struct {
 /* Solves n independent problems A_i x_i = phi_i (each its own lattice, Ls and masses) to tol
  * with FP32 CG and FP64 reliable updates (the CG of Eq. 3 per problem; batching many solves
  * has no counterpart in the paper).  All problems advance together: problems with the same
- * Ls share one concatenated site space, and one CG step of all of them is five kernel
- * launches per Ls group (stages A, B, A^dag, B^dag on persistent grids, then the update);
- * chunks of 16 steps of all groups are captured once as a CUDA graph and replayed, with the
- * per-problem FP64 reliable updates between replays.  stream: cudaStream_t.  per_solve (n entries, nullable) receives each
+ * Ls share one concatenated site space, and a chunk of 16 CG steps of all of them is, per Ls
+ * group, either one persistent cooperative kernel launch (five phases per step separated by
+ * grid barriers with bounded waits) or five launches per step (stages A, B, A^dag, B^dag on
+ * persistent grids, then the update), whichever the first chunks time faster; the chosen
+ * chunks of all groups are captured once as a CUDA graph and replayed, with the per-problem
+ * FP64 reliable updates between replays.  stream: cudaStream_t.  per_solve (n entries, nullable) receives each
  * problem's statistics.  Fields are host or device; the call keeps none of the caller's
  * pointers.  Returns DWF_ERR_ARG for n <= 0, a bad tolerance, an unsupported size or a NULL
- * field, DWF_ERR_NOT_CONVERGED if some problem misses tol within maxit steps. */
+ * field, DWF_ERR_NOT_CONVERGED if some problem misses tol within maxit steps, DWF_ERR_TIMEOUT if a
+ * bounded device-side wait gave up. */
 dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double tol, int maxit,
                            dwf_stats* per_solve, void* stream);
 

@@ -4,10 +4,11 @@
 // Problems with the same Ls share one concatenated site space (each problem padded to whole
 // 32-site tiles); every problem is one reduction/scalar segment with its own fifth-dimension
 // matrices, M5op coefficients, stop flag and CG scalars.  A chunk of 16 FP32 CG steps of every
-// problem of a group is one persistent, cooperative launch (batch_steps.cu: five phases per
-// step over all tiles, grid barriers with bounded waits); the grid size and the stages' link
-// staging are picked by timing the first chunks, and the chosen launches of all groups are
-// then captured once in a CUDA graph and replayed.  FP32 CG with FP64 reliable updates per
+// problem of a group is either one persistent, cooperative launch (batch_steps.cu: five
+// phases per step over all tiles, grid barriers with bounded waits) or five launches per step
+// (stages A, B, A^dag, B^dag on persistent grids, then the update); which one, the grid size
+// and the link staging are picked per group by timing the first chunks, and the chosen
+// launches of all groups are then captured once in a CUDA graph and replayed.  FP32 CG with FP64 reliable updates per
 // problem (the true residual is recomputed in FP64 when a problem's FP32 residual has dropped
 // by delta = 0.1, or at convergence), between replays.
 #include <chrono>
@@ -55,7 +56,8 @@ struct Group {
   unsigned* counter = nullptr; // [nseg]
   double* partial = nullptr;   // [ntiles]
   int grid = 0;                // autotuned persistent grid of the stage launches
-  int sgrid = 0, sgather = 0;  // persistent CG-step launch: grid, link staging (tuned)
+  int sgrid = 0, sgather = -1;  // persistent CG-step launch: grid, link staging (tuned;
+                                // gather -1: one launch per stage instead)
   unsigned* bar = nullptr;     // barrier counter of the persistent launch
   int* err = nullptr;          // set when a bounded device wait gives up
   int post_struct = 1;         // every problem has |beta/alpha| < 1: post by recurrences
@@ -807,11 +809,12 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
   }
   DWF_CUDA(cudaStreamSynchronize(B.st));
 
-  // a chunk of CG steps of every group: one persistent launch per group.  The first chunks
-  // time the candidate launches (grid of 1 or 2 CTAs per SM or the largest co-resident grid,
-  // links read directly or staged by TMA bulk copies); the fastest of each group is then
-  // captured once in a CUDA graph and replayed.  Groups whose fifth-dimension post cannot use
-  // the recurrences keep one launch per stage (a captured chunk of g_cg_step).
+  // a chunk of CG steps of every group: one persistent launch per group, or one launch per
+  // stage and update (g_cg_step, each stage with its own tuned variant).  The first chunks time
+  // the candidates (the stage launches; the persistent launch with a grid of 1 or 2 CTAs per
+  // SM or the largest co-resident grid, links read directly or staged by TMA bulk copies); the
+  // fastest of each group is then captured once in a CUDA graph and replayed.  Groups whose
+  // fifth-dimension post cannot use the recurrences keep the stage launches.
   const int chunk = 16;
   int dev = 0, nsm = 1;
   DWF_CUDA(cudaGetDevice(&dev));
@@ -828,6 +831,7 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
   for (size_t gi = 0; gi < B.groups.size(); gi++) {
     Group& G = *B.groups[gi];
     if (!G.post_struct) continue;
+    cands[gi].push_back({-1, 0});   // one launch per stage (gather -1)
     BatchStepArgs ba;
     g_step_args(G, chunk, wait_ns, ba);
     for (int gather : {G_REG, G_TMA}) {
@@ -838,7 +842,7 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
       if (cap > 2 * nsm) grids.push_back(cap);
       for (int g : grids) cands[gi].push_back({gather, (int)std::min<long>(g, G.ntiles)});
     }
-    if (cands[gi].empty()) G.post_struct = 0;   // cannot be resident: stage launches
+
   }
   size_t ntune = 0;
   for (auto& c : cands) ntune = std::max(ntune, c.size());
@@ -862,14 +866,14 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // a first un-captured step of the stage path sets its kernels' attributes
-  for (auto& G : B.groups)
-    if (!G->post_struct) DWF_TRY(g_cg_step(*G, B.st));
+  for (auto& G : B.groups) DWF_TRY(g_cg_step(*G, B.st));
   auto capture = [&]() -> dwf_status {
     DWF_CUDA(cudaStreamSynchronize(B.st));
     DWF_CUDA(cudaStreamBeginCapture(B.st, cudaStreamCaptureModeThreadLocal));
     for (auto& Gp : B.groups) {
       Group& G = *Gp;
-      dwf_status s = G.post_struct ? launch_chunk(G, G.sgather, G.sgrid) : stage_chunk(G);
+      dwf_status s = (G.post_struct && G.sgather >= 0) ? launch_chunk(G, G.sgather, G.sgrid)
+                                                        : stage_chunk(G);
       if (s != DWF_OK) {
         cudaStreamEndCapture(B.st, &graph);
         if (graph) cudaGraphDestroy(graph);
@@ -897,7 +901,8 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
       }
       const Cand& c = cands[gi][std::min(tune_round, cands[gi].size() - 1)];
       DWF_CUDA(cudaEventRecord(tev[0], B.st));
-      DWF_TRY(launch_chunk(G, c.gather, c.grid));
+      if (c.gather < 0) DWF_TRY(stage_chunk(G));
+      else DWF_TRY(launch_chunk(G, c.gather, c.grid));
       DWF_CUDA(cudaEventRecord(tev[1], B.st));
       DWF_CUDA(cudaEventSynchronize(tev[1]));
       float ms = 0.f;
