@@ -831,7 +831,12 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
   for (size_t gi = 0; gi < B.groups.size(); gi++) {
     Group& G = *B.groups[gi];
     if (!G.post_struct) continue;
-    cands[gi].push_back({-1, 0});   // one launch per stage (gather -1)
+    // DWF_BATCH_FORM=stages|persistent restricts the candidates to one form
+    const char* form = getenv("DWF_BATCH_FORM");
+    const bool only_stages = form && strcmp(form, "stages") == 0;
+    const bool only_persistent = form && strcmp(form, "persistent") == 0;
+    if (!only_persistent) cands[gi].push_back({-1, 0});   // one launch per stage (gather -1)
+    if (only_stages) continue;
     BatchStepArgs ba;
     g_step_args(G, chunk, wait_ns, ba);
     for (int gather : {G_REG, G_TMA}) {

@@ -30,8 +30,13 @@ def _problems(specs, seed):
     return out
 
 
+@pytest.mark.parametrize("form", ["tuned", "persistent", "stages"])
 @pytest.mark.parametrize("host_buffers", [False, True])
-def test_batch_matches_single_solves(host_buffers):
+def test_batch_matches_single_solves(host_buffers, form, monkeypatch):
+    """Each form of a chunk of CG steps: one persistent launch per Ls group, one launch per
+    stage, or whichever the tuner picks."""
+    if form != "tuned":
+        monkeypatch.setenv("DWF_BATCH_FORM", form)
     dwf = lib()
     probs = _problems(SMALL, 51)
     batch = []
@@ -53,10 +58,13 @@ def test_batch_matches_single_solves(host_buffers):
         assert rel(x, host(xs)) <= 1e-7
 
 
-def test_batch_64_uneven_problems():
+@pytest.mark.parametrize("form", ["tuned", "persistent"])
+def test_batch_64_uneven_problems(form, monkeypatch):
     """The 64-problem Moebius workload (lattices 8^4, 8^3x16, 12^4, 16^3x32; Ls 8/12/16;
     mf in [0.005, 0.05]; eps in [0.2, 0.4]; seed 4): every problem reaches 1e-10 and a sample
     agrees with single-problem solves."""
+    if form != "tuned":
+        monkeypatch.setenv("DWF_BATCH_FORM", form)
     dwf = lib()
     specs = inputs.batch_problems(64, 4)
     batch = []
