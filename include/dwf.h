@@ -154,6 +154,28 @@ dwf_status dwf_mspcg(dwf_t handle, const int block[4], int inner_iters, dwf_prec
                      dwf_prec middle, dwf_local_op local_op, int flexible, const void* phi,
                      void* x, double tol, int maxit, dwf_stats* stats);
 
+/* Stationary block iterations on A x = phi built from the same local solves (comparison
+ * solvers of Sec. 1.2 and Sec. 2.1; the paper reports the multisplitting iteration itself to
+ * converge slowly, Sec. 2.3, which is why it preconditions CG instead).  One sweep:
+ *   colours = 1 : the multisplitting iteration of Eq. 2: every block solves its own equation
+ *                 with the current solution outside it as the boundary value, all blocks at
+ *                 once: x <- x + M^-1 (phi - A x), M the direct sum of the A_s (Eq. 5);
+ *   colours = 2 : multiplicative Schwarz over the black-white checkerboard of blocks
+ *                 (colour (b_x + b_y + b_z + b_t) mod 2 of the block coordinates b_mu): the
+ *                 blocks of one colour solve, the residual is recomputed, then the other;
+ *   colours = 16: the same over the 2^4 checkerboard (colour sum_mu 2^mu (b_mu mod 2)).
+ * Each A_s^-1 is inner_iters local CG iterations from a zero guess in storage precision
+ * `inner` (FP16/BF16 with a unit-RMS scale), local_op as in dwf_mspcg; the outer vectors and
+ * the residual b - A x (recomputed after every colour) are FP64.  Stops when
+ * ||phi - A x|| <= tol ||phi|| (tol = 0: run maxit sweeps) or after maxit sweeps
+ * (DWF_ERR_NOT_CONVERGED); stats->iterations counts sweeps, history the relative residual
+ * after each sweep.  x: initial guess must be zero (overwritten).  Returns DWF_ERR_ARG for
+ * colours not in {1, 2, 16}, or a checkerboard whose block count in some direction is odd
+ * and larger than one (the colouring would not alternate across the periodic boundary). */
+dwf_status dwf_ms_solve(dwf_t handle, const int block[4], int inner_iters, dwf_prec inner,
+                        dwf_local_op local_op, int colours, const void* phi, void* x,
+                        double tol, int maxit, dwf_stats* stats);
+
 /* Gradient of the pseudofermion action S = phi^dag (Mpc^dag Mpc)^-1 phi with respect to every
  * link, in the PyTorch complex convention dS/dRe U + i dS/dIm U (links layout).  X may be the
  * solution A^-1 phi (even-half, complex128) or NULL, in which case it is solved internally

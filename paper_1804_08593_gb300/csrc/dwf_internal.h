@@ -74,6 +74,7 @@ struct SimdArgs;
 struct SimdLocal {
   bool exact = false;
   int nb = 0, NB = 0, ngroups = 0;
+  int nbk[4] = {1, 1, 1, 1};  // blocks per direction
   int nBE = 0, nE = 0, nO = 0;
   long sB = 0, sE = 0, sO = 0;
   uint32_t* nbrE = nullptr;   // [nE][8] -> O position or SIMD_ABSENT
@@ -266,9 +267,11 @@ dwf_status ensure_simd(dwf_ctx* h, Layout* lay, bool exact, SimdLocal** out);
 struct SimdFields {
   void *x, *p, *u, *r, *t, *y;
 };
+// ncol > 1: only the blocks of colour col solve (the others return x = 0): one colour of a
+// multiplicative Schwarz sweep (colours as in dwf_ms_solve).
 dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const void* r_outer,
                             int prec_outer, long Vp_outer, double num, const double* den,
-                            const SimdFields& F);
+                            const SimdFields& F, int ncol = 1, int col = 0);
 template <int P>
 cudaError_t simd_launch_p(const SimdArgs& a, int Ls, int v, int* grid_cap, int nsm, cudaStream_t st,
                           bool query);

@@ -67,6 +67,9 @@ struct SimdArgs {
   double hs_b;                   // hop scale of the last stage: -1/4, or -b/4 when D+ = b
   int trivial;                   // c == 0: D+ = b, no pre-op field u
   int l;                         // local iterations
+  int ncol, col;                 // Schwarz sweeps: only blocks of colour col (of ncol) solve;
+                                 // the others get r = 0 and so x = 0 (ncol = 1: every block)
+  int nbk[4];                    // blocks per direction (block b = b_x + nbk_x (b_y + ...))
   unsigned* ctr;                 // [nslots] barrier counters, zero at launch
   double* partial;               // [nslots][C][32] per-CTA, per-block partial sums
   unsigned long long wait_ns;
@@ -571,6 +574,20 @@ simd_local_kernel(const SimdArgs a) {
     const long eg0 = (long)g * 32;
     const long eg = eg0 + lane;   // this lane's block, as an element offset
     double rho, alpha = 0.0, beta = 0.0;
+    // this lane's block takes part in this call (Schwarz colour)
+    bool active = true;
+    if (a.ncol > 1) {
+      int bb = (int)(g * 32 + lane), bc[4];
+#pragma unroll
+      for (int m = 0; m < 4; m++) {
+        bc[m] = bb % a.nbk[m];
+        bb /= a.nbk[m];
+      }
+      const int colour = a.ncol == 2 ? (bc[0] + bc[1] + bc[2] + bc[3]) & 1
+                                     : (bc[0] & 1) | (bc[1] & 1) << 1 | (bc[2] & 1) << 2 |
+                                           (bc[3] & 1) << 3;
+      active = (colour == a.col);
+    }
     // ---- P0: r = f r_outer (gathered into the block layout), p = r, x = 0, u = D+ p
     {
       double f = a.num;
@@ -583,7 +600,7 @@ simd_local_kernel(const SimdArgs a) {
 #pragma unroll
         for (int j = 0; j < NSL; j++) {
           const int s = w + j * LSP;
-          if (o < 0) {
+          if (o < 0 || !active) {
             zero(v[j]);
           } else if (a.prec_outer == P64) {
             Spinor<double> q;

@@ -164,6 +164,7 @@ dwf_status ensure_simd(dwf_ctx* h, Layout* lay, bool exact, SimdLocal** out) {
   auto S = std::make_unique<SimdLocal>();
   S->exact = exact;
   S->nb = g.nblocks;
+  for (int m = 0; m < 4; m++) S->nbk[m] = g.nb[m];
   S->ngroups = (g.nblocks + 31) / 32;
   S->NB = 32 * S->ngroups;
   S->nBE = nBE;
@@ -333,9 +334,12 @@ static int simd_pick(SimdLocal* S, int prec, cudaStream_t st, bool capturing, in
 
 dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const void* r_outer,
                             int prec_outer, long Vp_outer, double num, const double* den,
-                            const SimdFields& F) {
+                            const SimdFields& F, int ncol, int col) {
   DWF_TRY(ensure_simd_links(h, S, prec));
   SimdArgs a{};
+  a.ncol = ncol;
+  a.col = col;
+  for (int m = 0; m < 4; m++) a.nbk[m] = S->nbk[m];
   a.NB = S->NB;
   a.nb = S->nb;
   a.nBE = S->nBE;

@@ -792,3 +792,129 @@ extern "C" dwf_status dwf_mspcg(dwf_t h, const int block[4], int inner_iters, dw
   dwf_status st2 = finish_output(h, x, dx, ub);
   return st2 != DWF_OK ? st2 : st;
 }
+
+// ---------------------------------------------------------------------------------------
+// Stationary block iterations: the multisplitting iteration (Sec. 2.1, Eq. 2) and the
+// multiplicative Schwarz sweeps over 2- and 16-colour checkerboards of blocks.
+// ---------------------------------------------------------------------------------------
+namespace dwf {
+
+static dwf_status run_ms(dwf_ctx* h, Layout* lay, Layout* layL, int l, int inner, bool exact,
+                         int ncol, const void* b_c128, void* x_c128, double tol, int maxit,
+                         dwf_stats* stats) {
+  Timer timer;
+  stats_init(stats);
+  const Geom& g = layL->g;
+  OpEngine E64;
+  DWF_TRY(E64.init(h, layL, P64, false));
+  DWF_TRY(ensure_reduction(h, g.Vp / 32 * 2 + 64, 64));
+  SimdLocal* S;
+  DWF_TRY(ensure_simd(h, lay, exact, &S));
+  const size_t f64 = field_bytes(g, P64);
+  void *b64, *x64, *r64, *z64, *t1, *t2, *t3;
+  DWF_TRY(h->ws->get("ms_b64", f64, &b64));
+  DWF_TRY(h->ws->get("ms_x64", f64, &x64));
+  DWF_TRY(h->ws->get("ms_r64", f64, &r64));
+  DWF_TRY(h->ws->get("ms_zm", f64, &z64));
+  DWF_TRY(h->ws->get("ms_t1", f64, &t1));
+  DWF_TRY(h->ws->get("ms_t2", f64, &t2));
+  DWF_TRY(h->ws->get("ms_t3", f64, &t3));
+  const size_t per = (size_t)h->Ls * 24 * real_bytes(inner);
+  SimdFields F{};
+  DWF_TRY(h->ws->get("ms_xi", per * S->sB, &F.x));
+  DWF_TRY(h->ws->get("ms_pi", per * S->sB, &F.p));
+  DWF_TRY(h->ws->get("ms_ui", per * S->sB, &F.u));
+  DWF_TRY(h->ws->get("ms_ri", per * S->sB, &F.r));
+  DWF_TRY(h->ws->get("ms_ti", per * S->sO, &F.t));
+  DWF_TRY(h->ws->get("ms_yi", per * S->sE, &F.y));
+  double* dsc;
+  DWF_TRY(h->ws->get("ms_scal", S_NSLOT * sizeof(double), (void**)&dsc));
+  DWF_TRY(pack_even(h, layL, b_c128, b64, P64, 1.0));
+  DWF_TRY(vop(E64, VOP_ZERO, nullptr, x64));
+  double bb, rr;
+  DWF_TRY(true_residual(E64, b64, nullptr, r64, t1, t2, t3, dsc, &bb));
+  if (!(bb > 0.0) || !std::isfinite(bb)) {
+    if (bb == 0.0) {
+      DWF_TRY(unpack_even(h, layL, x64, P64, x_c128, 1.0));
+      DWF_CUDA(cudaStreamSynchronize(h->stream));
+      return DWF_OK;
+    }
+    return set_error(DWF_ERR_BREAKDOWN, "source norm is not finite");
+  }
+  rr = bb;
+  const bool scaled = (inner == P16 || inner == PB16);
+  const double nreal = 24.0 * h->Ls * (double)(g.V / 2);
+  std::vector<double> hist;
+  int k = 0, applications = 0;
+  dwf_status status = set_error(DWF_ERR_NOT_CONVERGED, "maximum number of sweeps reached");
+  while (k < maxit && rr > tol * tol * bb) {
+    for (int c = 0; c < ncol; c++) {
+      // z = local solves of the blocks of colour c on the current residual (|r|^2 in S_TMP),
+      // x += z, r = b - A x
+      DWF_TRY(simd_local_solve(h, S, inner, l, r64, P64, g.Vp, scaled ? nreal : 1.0,
+                               scaled ? dsc + S_TMP : nullptr, F, ncol, c));
+      DWF_TRY(cast(E64, inner, F.x, z64, scaled ? nreal : 1.0, scaled ? dsc + S_TMP : nullptr,
+                   1, nullptr, RedArgs{}, nullptr, S->inv, S->sB));
+      DWF_TRY(vop(E64, VOP_AXPY, z64, x64, RedArgs{}, 1.0));
+      DWF_TRY(true_residual(E64, b64, x64, r64, t1, t2, t3, dsc, &rr));
+      applications++;
+    }
+    k++;
+    hist.push_back(std::sqrt(rr / bb));
+    if (!std::isfinite(rr)) {
+      status = set_error(DWF_ERR_BREAKDOWN, "residual is not finite");
+      break;
+    }
+  }
+  if (rr <= tol * tol * bb) status = DWF_OK;
+  DWF_TRY(check_device_error(h));
+  DWF_TRY(unpack_even(h, layL, x64, P64, x_c128, 1.0));
+  DWF_CUDA(cudaStreamSynchronize(h->stream));
+  if (stats) {
+    stats->iterations = k;
+    stats->inner_iterations = k * ncol * l;
+    stats->operator_applications = applications;
+    stats->true_residual = std::sqrt(rr / bb);
+    if (stats->history && stats->history_capacity > 0) {
+      const int n = std::min((int)hist.size(), stats->history_capacity);
+      for (int i = 0; i < n; i++) stats->history[i] = hist[i];
+      stats->history_len = n;
+    }
+    stats->seconds = timer.seconds();
+  }
+  return status;
+}
+
+}  // namespace dwf
+
+extern "C" dwf_status dwf_ms_solve(dwf_t h, const int block[4], int inner_iters,
+                                   dwf_prec inner, dwf_local_op local_op, int colours,
+                                   const void* phi, void* x, double tol, int maxit,
+                                   dwf_stats* stats) {
+  if (!h || !block || !phi || !x) return set_error(DWF_ERR_ARG, "null argument");
+  if (inner_iters < 1) return set_error(DWF_ERR_ARG, "inner_iters must be >= 1");
+  if (!(tol >= 0.0) || maxit < 0) return set_error(DWF_ERR_ARG, "bad tolerance or maxit");
+  if ((int)inner < 0 || (int)inner > 3) return set_error(DWF_ERR_ARG, "bad inner precision");
+  if (local_op != DWF_LOCAL_DROP && local_op != DWF_LOCAL_EXACT)
+    return set_error(DWF_ERR_ARG, "unknown local_op");
+  if (colours != 1 && colours != 2 && colours != 16)
+    return set_error(DWF_ERR_ARG, "colours must be 1, 2 or 16");
+  Layout* lay;
+  DWF_TRY(get_layout(h, block, &lay));
+  if (colours > 1)
+    for (int m = 0; m < 4; m++)
+      if (lay->g.nb[m] > 1 && lay->g.nb[m] % 2 != 0)
+        return set_error(DWF_ERR_ARG, "a checkerboard of blocks needs an even number of "
+                                      "blocks (or one) in every direction");
+  Layout* layL;
+  DWF_TRY(get_layout(h, h->dims, &layL));
+  const size_t ub = (size_t)h->Ls * (lay->g.V / 2) * 12 * 16;
+  void *db, *dx;
+  DWF_TRY(stage_buffer(h, "io_phi", phi, ub, true, &db));
+  DWF_TRY(stage_buffer(h, "io_x", x, ub, false, &dx));
+  dwf_status st = run_ms(h, lay, layL, inner_iters, (int)inner, local_op == DWF_LOCAL_EXACT,
+                         colours, db, dx, tol, maxit, stats);
+  if (st != DWF_OK && st != DWF_ERR_NOT_CONVERGED) return st;
+  dwf_status st2 = finish_output(h, x, dx, ub);
+  return st2 != DWF_OK ? st2 : st;
+}

@@ -28,7 +28,7 @@ LOCAL_DROP, LOCAL_EXACT = 0, 1
 EXPORTS = ("dwf_create", "dwf_update_links", "dwf_apply", "dwf_cg", "dwf_mspcg", "dwf_force",
            "dwf_action", "dwf_batch_solve", "dwf_last_error", "dwf_destroy", "dwf_version",
            "dwf_profile_enable", "dwf_profile_read", "dwf_mdagm_noalloc", "dwf_set_option",
-           "dwf_measure_peak")
+           "dwf_measure_peak", "dwf_ms_solve")
 OPT_WAIT_LIMIT_US, OPT_TEST_WAIT_PROBE = 0, 1
 
 
@@ -98,11 +98,13 @@ def load() -> ctypes.CDLL:
     lib.dwf_mdagm_noalloc.argtypes = [ctypes.POINTER(i), i, d, d, d, d, vp, vp, vp, i, vp]
     lib.dwf_profile_read.argtypes = [vp, ctypes.POINTER(KernelProfile), i, ctypes.POINTER(i)]
     lib.dwf_set_option.argtypes = [vp, i, d]
+    lib.dwf_ms_solve.argtypes = [vp, ctypes.POINTER(i), i, i, i, i, vp, vp, d, i,
+                                 ctypes.POINTER(Stats)]
     lib.dwf_measure_peak.argtypes = [i, vp, ctypes.POINTER(d)]
     for name in ("dwf_create", "dwf_update_links", "dwf_apply", "dwf_cg", "dwf_mspcg",
                  "dwf_force", "dwf_action", "dwf_batch_solve", "dwf_profile_enable",
                  "dwf_profile_read", "dwf_mdagm_noalloc", "dwf_set_option",
-                 "dwf_measure_peak"):
+                 "dwf_measure_peak", "dwf_ms_solve"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -225,6 +227,25 @@ def dwf_mspcg(h: Handle, block, inner_iters, inner, middle, phi, x, tol, maxit,
     s = load().dwf_mspcg(h.ptr, blk, int(inner_iters), _prec(inner), _prec(middle),
                          int(local_op), int(bool(flexible)), _ptr(phi), _ptr(x), float(tol),
                          int(maxit), ctypes.byref(st))
+    _check(s, () if raise_on_fail else (DWF_ERR_NOT_CONVERGED,))
+    out = st.as_dict()
+    out["status"] = s
+    return out
+
+
+def dwf_ms_solve(h: Handle, block, inner_iters, inner, colours, phi, x, tol, maxit,
+                 local_op=LOCAL_EXACT, history: int = 0, raise_on_fail=True):
+    """Stationary block iteration: colours 1 (multisplitting iteration), 2 or 16 (Schwarz)."""
+    st = Stats()
+    buf = None
+    if history:
+        buf = (ctypes.c_double * history)()
+        st.history = buf
+        st.history_capacity = history
+    blk = (ctypes.c_int * 4)(*[int(v) for v in block])
+    s = load().dwf_ms_solve(h.ptr, blk, int(inner_iters), _prec(inner), int(local_op),
+                            int(colours), _ptr(phi), _ptr(x), float(tol), int(maxit),
+                            ctypes.byref(st))
     _check(s, () if raise_on_fail else (DWF_ERR_NOT_CONVERGED,))
     out = st.as_dict()
     out["status"] = s
