@@ -66,11 +66,11 @@ def args_parse():
 
 
 # ------------------------------------------------------------------------------------------
-STAGE_SOURCES = ("stage.cuh", "dwf_device.cuh", "tc_m5.cuh")
+STAGE_SOURCES = ("stage.cuh", "dwf_device.cuh", "tc_m5.cuh", "local_kernel.cuh", "sync.cuh")
 
 
 def stage_sources_sha() -> str:
-    """First 16 hex digits of the SHA-256 of the stage-kernel sources."""
+    """First 16 hex digits of the SHA-256 of the operator-kernel sources (stages, local solves)."""
     import hashlib
     h = hashlib.sha256()
     for name in STAGE_SOURCES:
