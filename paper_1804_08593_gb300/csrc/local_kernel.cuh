@@ -341,21 +341,41 @@ __device__ __forceinline__ void simd_hop_out(Spinor<typename Prec<P>::acc> (&out
   hop_acc_out<P, simd_nsl<P>()>(h, out);
 }
 
-// buf[s][24][32] <-> the per-thread spinor of slice s
+// The fifth-dimension buffer <-> the per-thread spinor of slice s.  FP32 accumulation: float4
+// quads, buf[(s * 6 + q) * 32 + lane] = components 2q, 2q + 1 (re, im, re, im), so a warp moves
+// 512 contiguous bytes per quad; FP64: scalars, buf[(s * 24 + k) * 32 + lane].
 template <typename A>
 __device__ __forceinline__ void to_buf(A* buf, const Spinor<A>& v, int s, int lane) {
+  if constexpr (std::is_same<A, float>::value) {
+    float4* b4 = reinterpret_cast<float4*>(buf);
 #pragma unroll
-  for (int k = 0; k < 12; k++) {
-    buf[(s * 24 + 2 * k) * 32 + lane] = v.c[k].x;
-    buf[(s * 24 + 2 * k + 1) * 32 + lane] = v.c[k].y;
+    for (int q = 0; q < 6; q++)
+      b4[(s * 6 + q) * 32 + lane] =
+          make_float4(v.c[2 * q].x, v.c[2 * q].y, v.c[2 * q + 1].x, v.c[2 * q + 1].y);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      buf[(s * 24 + 2 * k) * 32 + lane] = v.c[k].x;
+      buf[(s * 24 + 2 * k + 1) * 32 + lane] = v.c[k].y;
+    }
   }
 }
 template <typename A>
 __device__ __forceinline__ void from_buf(Spinor<A>& v, const A* buf, int s, int lane) {
+  if constexpr (std::is_same<A, float>::value) {
+    const float4* b4 = reinterpret_cast<const float4*>(buf);
 #pragma unroll
-  for (int k = 0; k < 12; k++) {
-    v.c[k].x = buf[(s * 24 + 2 * k) * 32 + lane];
-    v.c[k].y = buf[(s * 24 + 2 * k + 1) * 32 + lane];
+    for (int q = 0; q < 6; q++) {
+      const float4 t = b4[(s * 6 + q) * 32 + lane];
+      v.c[2 * q] = {t.x, t.y};
+      v.c[2 * q + 1] = {t.z, t.w};
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      v.c[k].x = buf[(s * 24 + 2 * k) * 32 + lane];
+      v.c[k].y = buf[(s * 24 + 2 * k + 1) * 32 + lane];
+    }
   }
 }
 
@@ -363,61 +383,135 @@ __device__ __forceinline__ void from_buf(Spinor<A>& v, const A* buf, int s, int 
 // absorbed pre-op factor) or M5op^-dag D+^dag (DAG true).  Per chirality K is a cyclic shift
 // with a -mf corner, so M5op = la (1 + r S) is inverted by a one-sided recurrence plus the
 // Sherman-Morrison correction for the corner, kappa = r mf / (1 + mf (-r)^Ls).
+// FP32 accumulation: one work item is a quad of four columns of one chirality (q < 3: the
+// upper spins), run as two packed f32x2 column pairs; FP64: one column per item.
+template <int LS, bool DAG>
+__device__ __forceinline__ void post_recurrence_q(float* bufp, const Coef5<float>& C, int tid,
+                                                  int nt) {
+  float4* buf = reinterpret_cast<float4*>(bufp);
+  const float2 mr = bcast2(-C.r), inva = bcast2(C.inva);
+  const float2 b2 = bcast2(DAG ? C.db : C.pre * C.db), c2 = bcast2(DAG ? C.dc : C.pre * C.dc);
+  const float2 cw = bcast2(-C.mf * (DAG ? C.dc : C.pre * C.dc));   // the wall term's factor
+  for (int it = tid; it < 6 * 32; it += nt) {
+    const int q = it >> 5, l = it & 31;
+    const bool lower = ((q < 3) != DAG);
+    float2 v[LS][2];
+#pragma unroll
+    for (int t = 0; t < LS; t++) {
+      const float4 x = buf[(t * 6 + q) * 32 + l];
+      v[t][0] = make_float2(x.x, x.y);
+      v[t][1] = make_float2(x.z, x.w);
+    }
+    // D+ (or D+^dag) in place: w_t = b v_t + c v_{t-1} (lower; the wall: -mf v_{Ls-1}) or
+    // w_t = b v_t + c v_{t+1} (upper; the wall: -mf v_0)
+    auto dplus = [&](float2 (&vv)[LS][2], float2 bb, float2 cc, float2 cwall) {
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        if (lower) {
+          const float2 wrap = vv[LS - 1][h];
+#pragma unroll
+          for (int t = LS - 1; t > 0; t--) vv[t][h] = __ffma2_rn(cc, vv[t - 1][h], __fmul2_rn(bb, vv[t][h]));
+          vv[0][h] = __ffma2_rn(cwall, wrap, __fmul2_rn(bb, vv[0][h]));
+        } else {
+          const float2 wrap = vv[0][h];
+#pragma unroll
+          for (int t = 0; t + 1 < LS; t++) vv[t][h] = __ffma2_rn(cc, vv[t + 1][h], __fmul2_rn(bb, vv[t][h]));
+          vv[LS - 1][h] = __ffma2_rn(cwall, wrap, __fmul2_rn(bb, vv[LS - 1][h]));
+        }
+      }
+    };
+    if (DAG) dplus(v, b2, c2, cw);
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      if (lower) {
+#pragma unroll
+        for (int t = 1; t < LS; t++) v[t][h] = __ffma2_rn(mr, v[t - 1][h], v[t][h]);
+        const float2 e = __fmul2_rn(bcast2(C.kappa), v[LS - 1][h]);
+        float g = 1.f;
+#pragma unroll
+        for (int t = 0; t < LS; t++) {
+          v[t][h] = __fmul2_rn(__ffma2_rn(e, bcast2(g), v[t][h]), inva);
+          g *= -C.r;
+        }
+      } else {
+#pragma unroll
+        for (int t = LS - 2; t >= 0; t--) v[t][h] = __ffma2_rn(mr, v[t + 1][h], v[t][h]);
+        const float2 e = __fmul2_rn(bcast2(C.kappa), v[0][h]);
+        float g = 1.f;
+#pragma unroll
+        for (int t = LS - 1; t >= 0; t--) {
+          v[t][h] = __fmul2_rn(__ffma2_rn(e, bcast2(g), v[t][h]), inva);
+          g *= -C.r;
+        }
+      }
+    }
+    if (!DAG) dplus(v, b2, c2, cw);
+#pragma unroll
+    for (int t = 0; t < LS; t++)
+      buf[(t * 6 + q) * 32 + l] = make_float4(v[t][0].x, v[t][0].y, v[t][1].x, v[t][1].y);
+  }
+}
+
 template <typename A, int LS, bool DAG>
 __device__ __forceinline__ void post_recurrence(A* buf, const Coef5<A>& C, int tid, int nt) {
-  const A r = C.r, inva = C.inva, kappa = C.kappa;
-  const A b_ = C.db, c_ = C.dc, mfA = C.mf, pre = C.pre;
-  for (int col = tid; col < 24 * 32; col += nt) {
-    const int c = col >> 5, l = col & 31;
-    const bool lower = ((c < 12) != DAG);
-    A v[LS];
+  if constexpr (std::is_same<A, float>::value) {
+    post_recurrence_q<LS, DAG>(buf, C, tid, nt);
+    return;
+  } else {
+    const A r = C.r, inva = C.inva, kappa = C.kappa;
+    const A b_ = C.db, c_ = C.dc, mfA = C.mf, pre = C.pre;
+    for (int col = tid; col < 24 * 32; col += nt) {
+      const int c = col >> 5, l = col & 31;
+      const bool lower = ((c < 12) != DAG);
+      A v[LS];
 #pragma unroll
-    for (int t = 0; t < LS; t++) v[t] = buf[(t * 24 + c) * 32 + l];
-    if (DAG) {   // D+^dag first
-      A w[LS];
+      for (int t = 0; t < LS; t++) v[t] = buf[(t * 24 + c) * 32 + l];
+      if (DAG) {   // D+^dag first
+        A w[LS];
 #pragma unroll
-      for (int t = 0; t < LS; t++) {
-        const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
-                           : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
-        w[t] = b_ * v[t] + c_ * nb;
+        for (int t = 0; t < LS; t++) {
+          const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
+                             : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
+          w[t] = b_ * v[t] + c_ * nb;
+        }
+#pragma unroll
+        for (int t = 0; t < LS; t++) v[t] = w[t];
+      }
+      if (lower) {
+#pragma unroll
+        for (int t = 1; t < LS; t++) v[t] = v[t] - r * v[t - 1];
+        const A e = kappa * v[LS - 1];
+        A g = A(1);
+#pragma unroll
+        for (int t = 0; t < LS; t++) {
+          v[t] = (v[t] + e * g) * inva;
+          g *= -r;
+        }
+      } else {
+#pragma unroll
+        for (int t = LS - 2; t >= 0; t--) v[t] = v[t] - r * v[t + 1];
+        const A e = kappa * v[0];
+        A g = A(1);
+#pragma unroll
+        for (int t = LS - 1; t >= 0; t--) {
+          v[t] = (v[t] + e * g) * inva;
+          g *= -r;
+        }
+      }
+      if (!DAG) {   // then D+ (times the absorbed pre-op factor)
+        A w[LS];
+#pragma unroll
+        for (int t = 0; t < LS; t++) {
+          const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
+                             : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
+          w[t] = pre * (b_ * v[t] + c_ * nb);
+        }
+#pragma unroll
+        for (int t = 0; t < LS; t++) v[t] = w[t];
       }
 #pragma unroll
-      for (int t = 0; t < LS; t++) v[t] = w[t];
+      for (int t = 0; t < LS; t++) buf[(t * 24 + c) * 32 + l] = v[t];
     }
-    if (lower) {
-#pragma unroll
-      for (int t = 1; t < LS; t++) v[t] = v[t] - r * v[t - 1];
-      const A e = kappa * v[LS - 1];
-      A g = A(1);
-#pragma unroll
-      for (int t = 0; t < LS; t++) {
-        v[t] = (v[t] + e * g) * inva;
-        g *= -r;
-      }
-    } else {
-#pragma unroll
-      for (int t = LS - 2; t >= 0; t--) v[t] = v[t] - r * v[t + 1];
-      const A e = kappa * v[0];
-      A g = A(1);
-#pragma unroll
-      for (int t = LS - 1; t >= 0; t--) {
-        v[t] = (v[t] + e * g) * inva;
-        g *= -r;
-      }
-    }
-    if (!DAG) {   // then D+ (times the absorbed pre-op factor)
-      A w[LS];
-#pragma unroll
-      for (int t = 0; t < LS; t++) {
-        const A nb = lower ? (t > 0 ? v[t - 1] : -mfA * v[LS - 1])
-                           : (t + 1 < LS ? v[t + 1] : -mfA * v[0]);
-        w[t] = pre * (b_ * v[t] + c_ * nb);
-      }
-#pragma unroll
-      for (int t = 0; t < LS; t++) v[t] = w[t];
-    }
-#pragma unroll
-    for (int t = 0; t < LS; t++) buf[(t * 24 + c) * 32 + l] = v[t];
   }
 }
 
@@ -435,14 +529,28 @@ __device__ __forceinline__ void dplus_slices(Spinor<A> (&v)[NSL], A* buf, const 
     const int s = w + j * LSP;
     const int su = s + 1 < LS ? s + 1 : 0, sd = s > 0 ? s - 1 : LS - 1;
     const A fu = (s + 1 < LS) ? A(1) : -C.mf, fd = (s > 0) ? A(1) : -C.mf;
+    if constexpr (std::is_same<A, float>::value) {
+      const float4* b4 = reinterpret_cast<const float4*>(buf);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      const bool plus = k < 6;
-      const bool from_up = DAG ? plus : !plus;
-      const int sn = from_up ? su : sd;
-      const A f = from_up ? fu : fd;
-      v[j].c[k].x = C.db * v[j].c[k].x + C.dc * f * buf[(sn * 24 + 2 * k) * 32 + lane];
-      v[j].c[k].y = C.db * v[j].c[k].y + C.dc * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+      for (int q = 0; q < 6; q++) {   // components 2q, 2q + 1: P+ spins for q < 3
+        const bool from_up = DAG ? (q < 3) : (q >= 3);
+        const float4 t = b4[((from_up ? su : sd) * 6 + q) * 32 + lane];
+        const float f = C.dc * (from_up ? fu : fd);
+        v[j].c[2 * q].x = C.db * v[j].c[2 * q].x + f * t.x;
+        v[j].c[2 * q].y = C.db * v[j].c[2 * q].y + f * t.y;
+        v[j].c[2 * q + 1].x = C.db * v[j].c[2 * q + 1].x + f * t.z;
+        v[j].c[2 * q + 1].y = C.db * v[j].c[2 * q + 1].y + f * t.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        const bool plus = k < 6;
+        const bool from_up = DAG ? plus : !plus;
+        const int sn = from_up ? su : sd;
+        const A f = from_up ? fu : fd;
+        v[j].c[k].x = C.db * v[j].c[k].x + C.dc * f * buf[(sn * 24 + 2 * k) * 32 + lane];
+        v[j].c[k].y = C.db * v[j].c[k].y + C.dc * f * buf[(sn * 24 + 2 * k + 1) * 32 + lane];
+      }
     }
   }
   __syncthreads();
