@@ -79,7 +79,7 @@ struct SimdLocal {
   long sB = 0, sE = 0, sO = 0;
   uint32_t* nbrE = nullptr;   // [nE][8] -> O position or SIMD_ABSENT
   uint32_t* nbrO = nullptr;   // [nO][8] -> E position or SIMD_ABSENT
-  int* sch = nullptr;         // P1 (nO) | P2 (nE) | P3 (nO) | P4 (nBE) schedules
+  uint32_t* sch = nullptr;    // P1 (nO) | P2 (nE) | P3 (nO) | P4 (nBE) schedules
   int nsch[4] = {0, 0, 0, 0};
   long sch_off[4] = {0, 0, 0, 0};
   int* lexE = nullptr;        // [sE] element -> lexicographic site (-1: none)

@@ -49,7 +49,8 @@ struct SimdArgs {
   long sB, sE, sO;               // element strides of BE, E and O fields (positions * NB)
   const uint32_t* nbrE;          // [nE][8]: neighbour position in O, or SIMD_ABSENT
   const uint32_t* nbrO;          // [nO][8]: neighbour position in E, or SIMD_ABSENT
-  const int* sch[4];             // cost-sorted positions of P1 (O), P2 (E), P3 (O), P4 (BE)
+  const uint32_t* sch[4];        // cost-sorted entries of P1 (O), P2 (E), P3 (O), P4 (BE):
+                                 // position | live-hop mask << 24
   int nsch[4];
   const void* linksE;            // [8][NCHL][sE] links of the E sites (backward ones daggered)
   const void* linksO;            // [8][NCHL][sO]
@@ -156,16 +157,8 @@ __device__ __forceinline__ void simd_prefetch_links(uint4* lraw, const void* lin
   cp_async_commit();
 }
 
-// Live-hop mask of a table row: present entries (and, for be_only, entries < nBE).
-__device__ __forceinline__ uint32_t simd_live(const uint32_t* row, bool be_only, int nBE) {
-  uint32_t live = 0;
-#pragma unroll
-  for (int d = 0; d < 8; d++) {
-    const uint32_t j = __ldg(row + d);
-    if (j != SIMD_ABSENT && (!be_only || j < (uint32_t)nBE)) live |= 1u << d;
-  }
-  return live;
-}
+// Schedule entry: the position in the low 24 bits, the mask of its live hops above.
+constexpr uint32_t SIMD_POS_MASK = 0x00ffffffu;
 
 // The spinor of NCH 16-byte chunks q[0], q[qs], ... in the accumulation type.
 template <int P>
@@ -287,7 +280,7 @@ __device__ __forceinline__ void simd_hop(HopAcc<P>& acc, const uint32_t* row, ui
     for (int d = 0; d < 8; d++) {
       if (!((live >> d) & 1u)) continue;
       const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)w * NCH) * stride +
-                       (long)__ldg(row + d) * NB + eg;
+                       (long)row[d] * NB + eg;
       uint4 v[NCH];
 #pragma unroll
       for (int k = 0; k < NCH; k++) v[k] = __ldcg(q + k * stride);
@@ -298,7 +291,7 @@ __device__ __forceinline__ void simd_hop(HopAcc<P>& acc, const uint32_t* row, ui
     // flight ahead of the one being computed
     auto issue = [&](int d, int slot) {
       const uint4* q = reinterpret_cast<const uint4*>(in) + ((long)w * NCH) * stride +
-                       (long)__ldg(row + d) * NB + eg;
+                       (long)row[d] * NB + eg;
       uint4* dst = ring + (slot * NSL * NCH) * NT + tid;
 #pragma unroll
       for (int j = 0; j < NSL; j++)
@@ -648,31 +641,33 @@ simd_local_kernel(const SimdArgs a) {
     ++nbar;
     return slot_barrier(ctr, nbar * (unsigned)C, a.wait_ns, a.err);
   };
-  // One hop phase over the schedule `sch` (n positions) of output tables `tab`: the tile's
-  // links are prefetched one tile ahead into the idle raw buffer; `body(pos, row, live, lraw)`
-  // computes the tile.
-  auto phase = [&](const int* sch, int n, const uint32_t* tab, bool be_only, const void* links,
+  // One hop phase over the schedule `sch` (n entries) of output tables `tab`: the tile's links
+  // and its table row are copied one tile ahead into the idle buffers, and the schedule entry
+  // two tiles ahead is loaded while the current tile computes, so no global load sits between
+  // a tile's start and its first neighbour copy.  `body(pos, row, live, lraw)` computes the
+  // tile (row in shared memory).
+  __shared__ __align__(16) uint32_t rows_s[2][8];
+  auto phase = [&](const uint32_t* sch, int n, const uint32_t* tab, const void* links,
                    long lstride, long eg0, auto body) {
+    auto prefetch = [&](uint4* lbuf, uint32_t* rbuf, uint32_t ent) {
+      const int pos = (int)(ent & SIMD_POS_MASK);
+      if (tid < 2) cp_async16<false>(rbuf + 4 * tid, tab + pos * 8 + 4 * tid);
+      simd_prefetch_links<P>(lbuf, links, lstride, (long)pos * NB + eg0, ent >> 24, tid, NT);
+    };
+    uint32_t e_cur = ci < n ? __ldg(sch + ci) : 0u;
+    uint32_t e_nxt = ci + C < n ? __ldg(sch + ci + C) : 0u;
+    if (ci < n) prefetch(lraw0, rows_s[0], e_cur);
     int it = 0;
-    if (ci < n) {
-      const int pos = __ldg(sch + ci);
-      simd_prefetch_links<P>(lraw0, links, lstride, (long)pos * NB + eg0,
-                             simd_live(tab + pos * 8, be_only, a.nBE), tid, NT);
-    }
     for (int i = ci; i < n; i += C, it++) {
-      const int pos = __ldg(sch + i);
-      const uint32_t* row = tab + pos * 8;
-      const uint32_t live = simd_live(row, be_only, a.nBE);
+      const uint32_t e_nn = i + 2 * C < n ? __ldg(sch + i + 2 * C) : 0u;
       uint4* cur = (it & 1) ? lraw1 : lraw0;
       uint4* nxt = (it & 1) ? lraw0 : lraw1;
       cp_async_wait<0>();
-      __syncthreads();   // every thread's link copies of this tile have landed
-      if (i + C < n) {
-        const int pn = __ldg(sch + i + C);
-        simd_prefetch_links<P>(nxt, links, lstride, (long)pn * NB + eg0,
-                               simd_live(tab + pn * 8, be_only, a.nBE), tid, NT);
-      }
-      body(pos, row, live, cur);
+      __syncthreads();   // every thread's copies of this tile (links, row) have landed
+      if (i + C < n) prefetch(nxt, rows_s[(it + 1) & 1], e_nxt);
+      body((int)(e_cur & SIMD_POS_MASK), rows_s[it & 1], e_cur >> 24, cur);
+      e_cur = e_nxt;
+      e_nxt = e_nn;
     }
     cp_async_wait<0>();
     __syncthreads();
@@ -743,7 +738,7 @@ simd_local_kernel(const SimdArgs a) {
     for (int k = 0; k < a.l; k++) {
       const bool last = (k + 1 == a.l);
       // ---- P1: t = [D+ M5op^-1] Dh_oe (D+ p) on O
-      phase(a.sch[0], a.nsch[0], a.nbrO, true, a.linksO, sO, eg0,
+      phase(a.sch[0], a.nsch[0], a.nbrO, a.linksO, sO, eg0,
             [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
               Spinor<A> acc[NSL];
               simd_hop_out<P, LS, false, RS>(acc, row, live, pin1, sB, NB, eg, w, lraw, ring, lane, tid);
@@ -764,7 +759,7 @@ simd_local_kernel(const SimdArgs a) {
       {
         A nrm = A(0);
         const A hs = A(-0.25);
-        phase(a.sch[1], a.nsch[1], a.nbrE, false, a.linksE, sE, eg0,
+        phase(a.sch[1], a.nsch[1], a.nbrE, a.linksE, sE, eg0,
               [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
                 Spinor<A> acc[NSL];
                 simd_hop_out<P, LS, false, RS>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,
@@ -807,7 +802,7 @@ simd_local_kernel(const SimdArgs a) {
         break;
       }
       // ---- P3: s = [M5op^-dag D+^dag] Dh_oe^dag y on O
-      phase(a.sch[2], a.nsch[2], a.nbrO, false, a.linksO, sO, eg0,
+      phase(a.sch[2], a.nsch[2], a.nbrO, a.linksO, sO, eg0,
             [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
               Spinor<A> acc[NSL];
               simd_hop_out<P, LS, true, RS>(acc, row, live, a.y, sE, NB, eg, w, lraw, ring, lane, tid);
@@ -828,7 +823,7 @@ simd_local_kernel(const SimdArgs a) {
       {
         A nrm = A(0);
         const A al = A(alpha), hs = A(a.hs_b);
-        phase(a.sch[3], a.nsch[3], a.nbrE, false, a.linksE, sE, eg0,
+        phase(a.sch[3], a.nsch[3], a.nbrE, a.linksE, sE, eg0,
               [&](int pos, const uint32_t* row, uint32_t live, const uint4* lraw) {
                 Spinor<A> acc[NSL];
                 simd_hop_out<P, LS, true, RS>(acc, row, live, a.t, sO, NB, eg, w, lraw, ring, lane,

@@ -197,30 +197,36 @@ dwf_status ensure_simd(dwf_ctx* h, Layout* lay, bool exact, SimdLocal** out) {
     std::stable_sort(v.begin(), v.end(), [&](int a, int b) { return cost(a) > cost(b); });
     return v;
   };
-  auto liveO = [&](int i, bool be_only) {
-    int c = 0;
+  auto maskO = [&](int i, bool be_only) {
+    uint32_t m = 0;
     for (int d = 0; d < 8; d++) {
       const uint32_t j = nbrO[8 * i + d];
-      c += (j != SIMD_ABSENT && (!be_only || (int)j < nBE)) ? 1 : 0;
+      if (j != SIMD_ABSENT && (!be_only || (int)j < nBE)) m |= 1u << d;
     }
-    return c;
+    return m;
   };
-  auto liveE = [&](int i) {
-    int c = 0;
-    for (int d = 0; d < 8; d++) c += nbrE[8 * i + d] != SIMD_ABSENT ? 1 : 0;
-    return c;
+  auto maskE = [&](int i) {
+    uint32_t m = 0;
+    for (int d = 0; d < 8; d++)
+      if (nbrE[8 * i + d] != SIMD_ABSENT) m |= 1u << d;
+    return m;
   };
-  std::vector<int> sch;
-  const std::vector<int> s1 = sorted(S->nO, [&](int i) { return liveO(i, true); });
-  const std::vector<int> s2 = sorted(S->nE, [&](int i) { return liveE(i) + (i < nBE ? 3 : 0); });
-  const std::vector<int> s3 = sorted(S->nO, [&](int i) { return liveO(i, false); });
-  const std::vector<int> s4 = sorted(nBE, [&](int i) { return liveE(i); });
-  const std::vector<int>* ss[4] = {&s1, &s2, &s3, &s4};
-  for (int q = 0; q < 4; q++) {
-    S->nsch[q] = (int)ss[q]->size();
+  auto pop = [](uint32_t m) { return (int)__builtin_popcount(m); };
+  // schedule entries: position | live-hop mask << 24
+  if (std::max(S->nE, S->nO) > (int)SIMD_POS_MASK)
+    return set_error(DWF_ERR_ARG, "block halo sets too large for the local-solve schedule");
+  std::vector<uint32_t> sch;
+  auto append = [&](int q, const std::vector<int>& order, auto mask) {
+    S->nsch[q] = (int)order.size();
     S->sch_off[q] = (long)sch.size();
-    sch.insert(sch.end(), ss[q]->begin(), ss[q]->end());
-  }
+    for (int i : order) sch.push_back((uint32_t)i | mask(i) << 24);
+  };
+  append(0, sorted(S->nO, [&](int i) { return pop(maskO(i, true)); }),
+         [&](int i) { return maskO(i, true); });
+  append(1, sorted(S->nE, [&](int i) { return pop(maskE(i)) + (i < nBE ? 3 : 0); }), maskE);
+  append(2, sorted(S->nO, [&](int i) { return pop(maskO(i, false)); }),
+         [&](int i) { return maskO(i, false); });
+  append(3, sorted(nBE, [&](int i) { return pop(maskE(i)); }), maskE);
   // element -> site maps: element e = position * NB + block
   auto site_of = [&](const std::array<int, 4>& c, int blk) -> long {
     int bc[4], x[4];
