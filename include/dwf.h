@@ -208,11 +208,11 @@ typedef struct {
  * grid barriers with bounded waits) or five launches per step (stages A, B, A^dag, B^dag on
  * persistent grids, then the update), whichever the first chunks time faster; the chosen
  * chunks of all groups are captured once as a CUDA graph and replayed, with the per-problem
- * FP64 reliable updates between replays.  stream: cudaStream_t.  per_solve (n entries, nullable) receives each
- * problem's statistics.  Fields are host or device; the call keeps none of the caller's
- * pointers.  Returns DWF_ERR_ARG for n <= 0, a bad tolerance, an unsupported size or a NULL
- * field, DWF_ERR_NOT_CONVERGED if some problem misses tol within maxit steps, DWF_ERR_TIMEOUT if a
- * bounded device-side wait gave up. */
+ * FP64 reliable updates between replays.  stream: cudaStream_t.  per_solve (n entries,
+ * nullable) receives each problem's statistics.  Fields are host or device; the call keeps
+ * none of the caller's pointers.  Returns DWF_ERR_ARG for n <= 0, a bad tolerance, an
+ * unsupported size or a NULL field, DWF_ERR_NOT_CONVERGED if some problem misses tol within
+ * maxit steps, DWF_ERR_TIMEOUT if a bounded device-side wait gave up. */
 dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double tol, int maxit,
                            dwf_stats* per_solve, void* stream);
 

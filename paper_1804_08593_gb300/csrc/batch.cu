@@ -8,9 +8,9 @@
 // phases per step over all tiles, grid barriers with bounded waits) or five launches per step
 // (stages A, B, A^dag, B^dag on persistent grids, then the update); which one, the grid size
 // and the link staging are picked per group by timing the first chunks, and the chosen
-// launches of all groups are then captured once in a CUDA graph and replayed.  FP32 CG with FP64 reliable updates per
-// problem (the true residual is recomputed in FP64 when a problem's FP32 residual has dropped
-// by delta = 0.1, or at convergence), between replays.
+// launches of all groups are then captured once in a CUDA graph and replayed.  FP32 CG with
+// FP64 reliable updates per problem (the true residual is recomputed in FP64 when a problem's
+// FP32 residual has dropped by delta = 0.1, or at convergence), between replays.
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -595,9 +595,11 @@ dwf_status build_group(Batch& B, Group& G, const dwf_problem* pr) {
       dim3 grid((unsigned)((Vp + 127) / 128), 8), block(128);
       const double2* U = reinterpret_cast<const double2*>(B.staged_links);
       if (prec == P64)
-        batch_pack_links_kernel<P64><<<grid, block, 0, st>>>(U, G.links[pi][par], G.nbr[par], G.lex[par], G.lex[1 - par], G.tile_seg, dloff, Vp);
+        batch_pack_links_kernel<P64><<<grid, block, 0, st>>>(
+            U, G.links[pi][par], G.nbr[par], G.lex[par], G.lex[1 - par], G.tile_seg, dloff, Vp);
       else
-        batch_pack_links_kernel<P32><<<grid, block, 0, st>>>(U, G.links[pi][par], G.nbr[par], G.lex[par], G.lex[1 - par], G.tile_seg, dloff, Vp);
+        batch_pack_links_kernel<P32><<<grid, block, 0, st>>>(
+            U, G.links[pi][par], G.nbr[par], G.lex[par], G.lex[1 - par], G.tile_seg, dloff, Vp);
       DWF_CUDA(cudaGetLastError());
     }
   }
