@@ -430,6 +430,8 @@ def run_ours(a):
     achieved = top["bytes"] / top["launches"] / (top["ms"] / top["launches"] / 1e3) / 1e9
     hop = [k for k in prof if k["name"].startswith("hop_")]
     hop_ms = sum(k["ms"] for k in hop)
+    hop32 = [k for k in hop if k["name"].startswith("hop_f32")]
+    hop32_ms = sum(k["ms"] for k in hop32)
     total_ms = sum(k["ms"] for k in prof)
 
     # end to end through the C ABI with host buffers (links in, source in, solution out)
@@ -533,7 +535,13 @@ def run_ours(a):
                   "reliable_updates": s0["reliable_updates"], "true_residual": s0["true_residual"]},
         "dslash": {"hbm_gbs": sum(k["bytes"] for k in hop) / (hop_ms / 1e3) / 1e9,
                    "gflops": sum(k["flops"] for k in hop) / (hop_ms / 1e3) / 1e9,
-                   "share_of_step": hop_ms / total_ms},
+                   "share_of_step": hop_ms / total_ms,
+                   "classes": "every outer-operator stage of the solve (FP32, and the FP64 "
+                              "reliable updates, which the FP64 ALU bounds)",
+                   "f32": {"hbm_gbs": sum(k["bytes"] for k in hop32) / (hop32_ms / 1e3) / 1e9,
+                           "gflops": sum(k["flops"] for k in hop32) / (hop32_ms / 1e3) / 1e9,
+                           "frac_of_hbm": (sum(k["bytes"] for k in hop32) / (hop32_ms / 1e3)
+                                           / 1e9 / pk["hbm_gbs"])} if hop32_ms > 0 else None},
         "roofline": {"bound": "hbm", "kernel": top["name"], "achieved": achieved,
                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                      "peak_kind": pk_kind,

@@ -272,6 +272,9 @@ struct SimdFields {
 dwf_status simd_local_solve(dwf_ctx* h, SimdLocal* S, int prec, int l, const void* r_outer,
                             int prec_outer, long Vp_outer, double num, const double* den,
                             const SimdFields& F, int ncol = 1, int col = 0);
+// True once the local solver's launch variant for this storage precision is fixed (timed by
+// the tuner, forced by DWF_LOCAL_VARIANT, or FP64's single variant).
+bool simd_variant_decided(const SimdLocal* S, int prec);
 template <int P>
 cudaError_t simd_launch_p(const SimdArgs& a, int Ls, int v, int* grid_cap, int nsm, cudaStream_t st,
                           bool query);

@@ -24,10 +24,18 @@ static cudaError_t launch_v(const SimdArgs& a, int* grid_cap, int nsm, cudaStrea
     *grid_cap = per_sm * nsm;
     return cudaSuccess;
   }
-  SimdArgs b = a;
-  void* args[] = {&b};
-  return cudaLaunchCooperativeKernel((const void*)k, dim3((unsigned)(a.nslots * a.C)),
-                                     dim3(32, LS / simd_nsl<P>()), args, smem, st);
+  // a cooperative launch through the extensible API (capturable in a CUDA graph)
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(a.nslots * a.C));
+  cfg.blockDim = dim3(32, LS / simd_nsl<P>());
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 template <int P, int LS>

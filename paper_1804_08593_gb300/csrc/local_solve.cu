@@ -288,6 +288,15 @@ static cudaError_t simd_launch(int prec, const SimdArgs& a, int Ls, int v, int* 
 // current choice.  DWF_LOCAL_VARIANT=<v> forces variant v.
 constexpr int SIMD_NV = 3, SIMD_TUNE_ROUNDS = 4;
 
+bool simd_variant_decided(const SimdLocal* S, int prec) {
+  if (prec == P64) return true;
+  if (const char* f = getenv("DWF_LOCAL_VARIANT")) {
+    const int v = atoi(f);
+    if (v >= 0 && v < SIMD_NV) return true;
+  }
+  return S->tune_chosen[prec] >= 0;
+}
+
 static int simd_pick(SimdLocal* S, int prec, cudaStream_t st, bool capturing, int* timed) {
   *timed = -1;
   if (prec == P64) return 0;

@@ -442,6 +442,32 @@ static dwf_status precondition_stages(const OpEngine& Em, const OpEngine& Ei, co
                                       const InnerVectors& iv, double* dsc, double* blk, int nb,
                                       int l);
 
+// The preconditioner step of the persistent local solver (the local solves' launch and the
+// reductions that follow it) as a CUDA graph: captured once the solver's launch variant is
+// decided (never while the per-launch profiler is on, whose events must be recorded per
+// launch), then replayed by every later preconditioner call of the solve.  Every argument of
+// the step (buffers, scalar slots, sizes) is the same on every call.  DWF_PRECOND_GRAPH=0
+// issues the launches directly.
+struct PcGraph {
+  cudaGraphExec_t exec = nullptr;
+  bool tried = false;
+  ~PcGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+static bool pc_graph_enabled(dwf_ctx* h, const InnerVectors& iv) {
+  const char* e = getenv("DWF_PRECOND_GRAPH");
+  if (e && strcmp(e, "0") == 0) return false;
+  if (h->prof.on || !iv.simd || !simd_variant_decided(iv.simd, iv.prec)) return false;
+  // the legacy default stream cannot be captured: handles created without a stream launch
+  // directly
+  if (h->stream == nullptr || h->stream == cudaStreamLegacy) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(h->stream, &cs) == cudaSuccess &&
+         cs == cudaStreamCaptureStatusNone;
+}
+
 // z = M^-1 r approximated by l local CG iterations per block from a zero guess (Eqs. 4-5),
 // with every block-local dot product reduced per block; then <r, z> (FR) or the
 // Polak-Ribiere numerator is reduced and beta is finalised on the device.
@@ -449,7 +475,7 @@ static dwf_status precondition_stages(const OpEngine& Em, const OpEngine& Ei, co
 // the Fletcher-Reeves beta) is reduced from the local solution directly.
 static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const void* r, void* z,
                                const InnerVectors& iv, double* dsc, double* blk, int nb, int l,
-                               bool flexible, const void* rold, ZSrc& zs) {
+                               bool flexible, const void* rold, ZSrc& zs, PcGraph* pg) {
   const int ip = iv.prec;
   const bool scaled = (ip == P16 || ip == PB16);
   const double nreal = 24.0 * Em.h->Ls * (double)(Em.g().V / 2);
@@ -458,9 +484,6 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
   long zvp = 0;
   double zbytes = 0.0;
   if (iv.simd) {
-    const SimdFields F{iv.xi, iv.pi, iv.ui, iv.ri, iv.ti, iv.yi};
-    DWF_TRY(simd_local_solve(Em.h, iv.simd, ip, l, r, Em.prec, Em.g().Vp,
-                             scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, F));
     zmap = iv.simd->inv;
     zvp = iv.simd->sB;
     zbytes = (double)Em.h->Ls * (double)iv.simd->sB * 24.0 * (double)real_bytes(ip);
@@ -471,12 +494,58 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
     zvp = Ei.g().Vp;
     zbytes = (double)field_bytes(Ei.g(), Ei.prec);
   }
+  // the device work after the stage-launched local solves, or all of it for the persistent
+  // local solver
+  auto issue = [&]() -> dwf_status {
+    if (iv.simd) {
+      const SimdFields F{iv.xi, iv.pi, iv.ui, iv.ri, iv.ti, iv.yi};
+      DWF_TRY(simd_local_solve(Em.h, iv.simd, ip, l, r, Em.prec, Em.g().Vp,
+                               scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, F));
+    }
+    if (!flexible) {
+      RedArgs rz = Em.red(FIN_BETA, nullptr);
+      rz.rho = dsc + S_RHO;
+      rz.beta = dsc + S_BETA;
+      DWF_TRY(cast(Em, ip, iv.xi, nullptr, scaled ? nreal : 1.0,
+                   scaled ? dsc + S_RR : nullptr, 1, r, rz, nullptr, zmap, zvp));
+    } else {
+      DWF_TRY(cast(Em, ip, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
+                   r, Em.red(FIN_STORE, dsc + S_RZNEW), nullptr, zmap, zvp));
+      DWF_TRY(vop(Em, VOP_DOT, rold, z, Em.red(FIN_STORE, dsc + S_TMP)));
+      pr_beta_kernel<<<1, 1, 0, Em.h->stream>>>(dsc);
+      DWF_CUDA(cudaGetLastError());
+    }
+    return DWF_OK;
+  };
+  cudaStream_t st = Em.h->stream;
+  if (pg && pg->exec) {
+    DWF_CUDA(cudaGraphLaunch(pg->exec, st));
+  } else if (pg && !pg->tried && pc_graph_enabled(Em.h, iv)) {
+    pg->tried = true;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaGetLastError();
+      return precondition(Em, Ei, r, z, iv, dsc, blk, nb, l, flexible, rold, zs, nullptr);
+    }
+    const dwf_status s_issue = issue();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(st, &graph);
+    cudaError_t e_inst = cudaErrorUnknown;
+    if (s_issue == DWF_OK && e_end == cudaSuccess && graph)
+      e_inst = cudaGraphInstantiate(&pg->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (s_issue != DWF_OK) return s_issue;
+    if (e_end != cudaSuccess || e_inst != cudaSuccess) {
+      // not capturable here: nothing of the step ran, so issue it directly (and from now on)
+      cudaGetLastError();
+      pg->exec = nullptr;
+      DWF_TRY(issue());
+    } else {
+      DWF_CUDA(cudaGraphLaunch(pg->exec, st));
+    }
+  } else {
+    DWF_TRY(issue());
+  }
   if (!flexible) {
-    RedArgs rz = Em.red(FIN_BETA, nullptr);
-    rz.rho = dsc + S_RHO;
-    rz.beta = dsc + S_BETA;
-    DWF_TRY(cast(Em, ip, iv.xi, nullptr, scaled ? nreal : 1.0,
-                 scaled ? dsc + S_RR : nullptr, 1, r, rz, nullptr, zmap, zvp));
     zs.src = iv.xi;
     zs.prec = ip;
     zs.map = zmap;
@@ -486,11 +555,6 @@ static dwf_status precondition(const OpEngine& Em, const OpEngine& Ei, const voi
     zs.bytes = zbytes;
   } else {
     zs = ZSrc{};
-    DWF_TRY(cast(Em, ip, iv.xi, z, scaled ? nreal : 1.0, scaled ? dsc + S_RR : nullptr, 1,
-                 r, Em.red(FIN_STORE, dsc + S_RZNEW), nullptr, zmap, zvp));
-    DWF_TRY(vop(Em, VOP_DOT, rold, z, Em.red(FIN_STORE, dsc + S_TMP)));
-    pr_beta_kernel<<<1, 1, 0, Em.h->stream>>>(dsc);
-    DWF_CUDA(cudaGetLastError());
   }
   return DWF_OK;
 }
@@ -655,7 +719,8 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
   DWF_TRY(vop(Em, VOP_ZERO, nullptr, pm));
   if (flex) DWF_TRY(vop(Em, VOP_ZERO, nullptr, rold));
   ZSrc zs;
-  DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold, zs));
+  PcGraph pg;
+  DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold, zs, &pg));
   // x += alpha p of an outer iteration is deferred into the next update of p (one pass over
   // x and p instead of two) unless a reliable update needs x first
   bool x_pending = false;
@@ -737,7 +802,7 @@ static dwf_status run_mspcg(dwf_ctx* h, Layout* lay, Layout* layL, int l, int in
       DWF_TRY(vop(Em, VOP_ZERO, nullptr, xm));
       anchor = rr64;
     }
-    DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold, zs));
+    DWF_TRY(precondition(Em, Ei, rm, zm, iv, dsc, blk, nbk, l, flex, rold, zs, &pg));
     inner_total += l;
     DWF_TRY(update_p());
   }

@@ -311,6 +311,32 @@ def test_mspcg_mixed_multi_tile_blocks_true_residual(name, inner):
     assert o.true_residual(U, host(x), phi, p) <= 1.5e-10
 
 
+@pytest.mark.parametrize("flexible", [False, True])
+def test_mspcg_preconditioner_graph_replays_the_direct_launches(flexible, monkeypatch):
+    """The preconditioner step of the persistent local solver is captured in a CUDA graph once
+    its launch variant is fixed (forced here, so from the first call) and replayed on every
+    later call of a handle with its own stream: the solve must be bit for bit the one the
+    direct launches give, and reach the oracle-recomputed true residual."""
+    import torch
+    monkeypatch.setenv("DWF_LOCAL_VARIANT", "0")
+    dwf = lib()
+    p, U, phi, blk, l, n = multi_tile("mobius_12x6x6x6_ls8_b6")
+    stream = torch.cuda.Stream()   # the legacy default stream cannot be captured
+    h = dwf.dwf_create(p.dims, p.Ls, p.M5, p.mf, p.b, p.c, cuda(U), stream)
+    out = {}
+    for graph in ("1", "0"):
+        monkeypatch.setenv("DWF_PRECOND_GRAPH", graph)
+        x = cuda(np.zeros_like(phi))
+        st = dwf.dwf_mspcg(h, blk, l, "f16", "f32", cuda(phi), x, 1e-10, 5000,
+                           local_op=dwf.LOCAL_EXACT, flexible=flexible, history=5000)
+        out[graph] = (st, host(x))
+    (sg, xg), (sd, xd) = out["1"], out["0"]
+    assert sg["iterations"] == sd["iterations"] and sg["iterations"] > 2
+    assert sg["history"] == sd["history"]
+    assert np.array_equal(xg, xd)
+    assert o.true_residual(U, xg, phi, p) <= 1.5e-10
+
+
 def test_cg_lanczos_kappa_matches_dense_spectrum():
     """The CG coefficients recorded by dwf_cg (residual norms and curvatures <p, A p>) give
     the Lanczos tridiagonal of A; its extreme eigenvalues are those of the dense A built by
