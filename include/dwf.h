@@ -206,9 +206,10 @@ typedef struct {
  * Ls share one concatenated site space, and a chunk of 16 CG steps of all of them is, per Ls
  * group, either one persistent cooperative kernel launch (five phases per step separated by
  * grid barriers with bounded waits) or five launches per step (stages A, B, A^dag, B^dag on
- * persistent grids, then the update), whichever the first chunks time faster; the chosen
- * chunks of all groups are captured once as a CUDA graph and replayed, with the per-problem
- * FP64 reliable updates between replays.  stream: cudaStream_t.  per_solve (n entries,
+ * persistent grids, then the update), whichever the first chunks time faster (the choice is
+ * kept for later calls on the same problem mix); the chosen chunks of all groups are captured
+ * once as a CUDA graph and replayed, with the per-problem FP64 reliable updates between
+ * replays.  stream: cudaStream_t.  per_solve (n entries,
  * nullable) receives each problem's statistics.  Fields are host or device; the call keeps
  * none of the caller's pointers.  Returns DWF_ERR_ARG for n <= 0, a bad tolerance, an
  * unsupported size or a NULL field, DWF_ERR_NOT_CONVERGED if some problem misses tol within

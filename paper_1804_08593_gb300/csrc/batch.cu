@@ -7,8 +7,9 @@
 // problem of a group is either one persistent, cooperative launch (batch_steps.cu: five
 // phases per step over all tiles, grid barriers with bounded waits) or five launches per step
 // (stages A, B, A^dag, B^dag on persistent grids, then the update); which one, the grid size
-// and the link staging are picked per group by timing the first chunks, and the chosen
-// launches of all groups are then captured once in a CUDA graph and replayed.  FP32 CG with
+// and the link staging are picked per group by timing the first chunks (and kept for later
+// calls on the same problem mix), and the chosen launches of all groups are then captured
+// once in a CUDA graph and replayed.  FP32 CG with
 // FP64 reliable updates per problem (the true residual is recomputed in FP64 when a problem's
 // FP32 residual has dropped by delta = 0.1, or at convergence), between replays.
 #include <chrono>
@@ -18,6 +19,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <vector>
 
@@ -700,6 +702,24 @@ dwf_status autotune(Group& G, cudaStream_t st) {
   return DWF_OK;
 }
 
+// The chunk form picked for a group, kept across calls: the same problem mix (Ls, sizes of
+// the problems in order, and the DWF_BATCH_FORM restriction) reuses it instead of timing the
+// candidates again.
+struct ChunkChoice {
+  int gather, grid;
+};
+std::mutex g_chunk_mu;
+std::map<std::string, ChunkChoice> g_chunk_cache;
+
+std::string chunk_key(const Batch& B, const Group& G, const char* form) {
+  std::string k = std::to_string(G.Ls) + "|" + (form ? form : "") + "|";
+  for (int q : G.ids) {
+    const Prob& P = B.probs[q];
+    for (int m = 0; m < 4; m++) k += std::to_string(P.dims[m]) + (m < 3 ? "x" : ",");
+  }
+  return k;
+}
+
 }  // namespace
 }  // namespace dwf
 
@@ -830,6 +850,7 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
     int gather, grid;
   };
   std::vector<std::vector<Cand>> cands(B.groups.size());
+  std::vector<std::string> keys(B.groups.size());
   for (size_t gi = 0; gi < B.groups.size(); gi++) {
     Group& G = *B.groups[gi];
     if (!G.post_struct) continue;
@@ -837,6 +858,16 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
     const char* form = getenv("DWF_BATCH_FORM");
     const bool only_stages = form && strcmp(form, "stages") == 0;
     const bool only_persistent = form && strcmp(form, "persistent") == 0;
+    keys[gi] = chunk_key(B, G, form);
+    {
+      std::lock_guard<std::mutex> lk(g_chunk_mu);
+      auto it = g_chunk_cache.find(keys[gi]);
+      if (it != g_chunk_cache.end()) {   // decided by an earlier call on this problem mix
+        G.sgather = it->second.gather;
+        G.sgrid = it->second.grid;
+        continue;
+      }
+    }
     if (!only_persistent) cands[gi].push_back({-1, 0});   // one launch per stage (gather -1)
     if (only_stages) continue;
     BatchStepArgs ba;
@@ -902,8 +933,9 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
     }
     for (size_t gi = 0; gi < B.groups.size(); gi++) {
       Group& G = *B.groups[gi];
-      if (!G.post_struct) {
-        DWF_TRY(stage_chunk(G));
+      if (!G.post_struct || cands[gi].empty()) {   // stage launches only, or decided earlier
+        if (G.post_struct && G.sgather >= 0) DWF_TRY(launch_chunk(G, G.sgather, G.sgrid));
+        else DWF_TRY(stage_chunk(G));
         continue;
       }
       const Cand& c = cands[gi][std::min(tune_round, cands[gi].size() - 1)];
@@ -919,12 +951,16 @@ extern "C" dwf_status dwf_batch_solve(int n, const dwf_problem* problems, double
     if (++tune_round == ntune) {
       for (size_t gi = 0; gi < B.groups.size(); gi++) {
         Group& G = *B.groups[gi];
-        if (!G.post_struct) continue;
+        if (!G.post_struct || cands[gi].empty()) continue;
         size_t best = 0;
         for (size_t k = 1; k < tuned[gi].size(); k++)
           if (tuned[gi][k] < tuned[gi][best]) best = k;
         G.sgather = cands[gi][best].gather;
         G.sgrid = cands[gi][best].grid;
+        {
+          std::lock_guard<std::mutex> lk(g_chunk_mu);
+          g_chunk_cache[keys[gi]] = {G.sgather, G.sgrid};
+        }
         if (getenv("DWF_TUNE_LOG")) {
           fprintf(stderr, "dwf tune batch Ls%d tiles %ld:", G.Ls, G.ntiles);
           for (size_t k = 0; k < tuned[gi].size(); k++)

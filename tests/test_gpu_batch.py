@@ -34,7 +34,8 @@ def _problems(specs, seed):
 @pytest.mark.parametrize("host_buffers", [False, True])
 def test_batch_matches_single_solves(host_buffers, form, monkeypatch):
     """Each form of a chunk of CG steps: one persistent launch per Ls group, one launch per
-    stage, or whichever the tuner picks."""
+    stage, or whichever the tuner picks.  The second call of each form (host buffers after
+    device buffers, same problems) reuses the form the first one picked."""
     if form != "tuned":
         monkeypatch.setenv("DWF_BATCH_FORM", form)
     dwf = lib()
