@@ -628,7 +628,7 @@ simd_local_kernel(const SimdArgs a) {
   __shared__ A red[LSP][32];
   __shared__ double sc[32];
   const int lane = threadIdx.x, w = threadIdx.y, tid = lane + 32 * w;
-  const int C = a.C, slot = blockIdx.x / C, ci = blockIdx.x % C;
+  const int C = a.C, slot = blockIdx.x % a.nslots, ci = blockIdx.x / a.nslots;
   if (slot >= a.nslots) return;
   unsigned* ctr = a.ctr + slot;
   double* part = a.partial + (long)slot * C * 32;
